@@ -1,0 +1,151 @@
+/*
+ * histretinex.h -- C ABI of the GB300 (sm_103a) HistRetinex library.
+ *
+ * HistRetinex (Zhao et al., arXiv 2510.21100) enhances a low-light RGB image in the
+ * histogram domain.  One call runs the whole per-image pipeline on the GPU:
+ *
+ *   1. V = max(r, g, b), the HSV value channel the paper enhances (Sec. II preamble);
+ *      its K-bin count histogram H_C(S) (Eq. 3) and the histogram H_C(grad S) of its
+ *      gradient image (Algorithm 1 initialisation; 3x3 Sobel magnitude, replicate border,
+ *      rounded half up, clipped to K-1);
+ *   2. the two-level optimisation of Sec. III.B: class map of the histogram location
+ *      matrix (Eq. 7 and the definition under Eq. 10), weights of the histogram count
+ *      matrix (Eq. 6, Eq. 11), reflectance update (Eq. 13), illumination update (Eq. 12),
+ *      renormalisation (Eq. 14, Eq. 15), iterated as Algorithm 1;
+ *   3. histogram reprocessing (Sec. III.C): gamma on the illumination location
+ *      histogram (Eq. 17), new location matrix (Eq. 18), index_1 (Eq. 19) and the
+ *      enhanced histogram (Eq. 20);
+ *   4. histogram matching of V to that histogram as a K-entry LUT (Sec. III.C, last
+ *      paragraph): LUT[s] = smallest z with CT(z) * N >= CS(s) * CT(K-1);
+ *   5. the per-pixel apply: V' = LUT[V], each channel c -> round_half_up(c * V' / V),
+ *      which keeps hue and saturation (Sec. II preamble; Sec. IV.A on methods that
+ *      stretch all three channels); a black pixel becomes grey (V', V', V').
+ *
+ * Data layout: images are interleaved RGB, row-major, 3 channels per pixel, each
+ * channel one byte (elem_bytes = 1, uint8) or a little-endian uint16 (elem_bytes = 2,
+ * values < K, e.g. 12-bit data with K = 4096).  Rows are `pitch` bytes apart
+ * (pitch >= 3 * width * elem_bytes).  Input and output may be the same buffer.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ * Device-side calls are asynchronous on that stream; argument errors are returned
+ * synchronously; errors found by the kernels (a level >= K, a timed-out wait) are
+ * recorded in a device status word and returned by histretinex_sync_status().
+ *
+ * Ownership: the caller owns every image buffer; the context owns its device
+ * workspace and per-K tables and frees them in histretinex_destroy().  A context is
+ * bound to one device and must not be used from two host threads at once.
+ */
+#ifndef HISTRETINEX_H
+#define HISTRETINEX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HR_OK = 0,
+  HR_ERR_INVALID_ARG = 1,  /* a bad pointer, size, pitch or parameter */
+  HR_ERR_UNSUPPORTED = 2,  /* a valid request this build does not handle (see each call) */
+  HR_ERR_OOM = 3,          /* device or host allocation failed */
+  HR_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+  HR_ERR_RANGE = 5,        /* an image held a level >= K */
+  HR_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up */
+} hr_status;
+
+typedef enum {
+  HR_PREC_FP64 = 0,        /* the plain form: the K-dimensional solve in FP64 */
+  HR_PREC_FP32 = 1         /* reduced precision: solve sums in FP32 (histograms, CDFs exact; LUT compare in FP64) */
+} hr_precision;
+
+enum {
+  HR_FLAG_FIXED_ITERS = 1u, /* always run max_iter iterations of Algorithm 1 (ignore eps) */
+  HR_FLAG_DEBUG_OUT = 2u,   /* keep per-image intermediates for histretinex_get_debug() */
+  HR_FLAG_STAGE_TIMING = 4u /* record CUDA events around each pipeline stage (histretinex_stage_times) */
+};
+
+/* Method parameters.  alpha, beta: weights of the illumination and reflectance priors
+ * (Eq. 9); gamma: Eq. 17; eps, max_iter: stopping threshold and iteration cap T of
+ * Algorithm 1 (stop when both squared changes are <= eps, or after max_iter).
+ * K must be a power of two in [8, 4096]; elem_bytes = 1 needs K <= 256. */
+typedef struct {
+  int K;
+  double alpha;
+  double beta;
+  double gamma;
+  double eps;
+  int max_iter;
+  int precision;   /* hr_precision */
+  unsigned flags;  /* HR_FLAG_* */
+} hr_params;
+
+typedef struct hr_ctx hr_ctx;
+
+/* Fills *p with the defaults: K = 256, alpha = beta = 1e-3, gamma = 2.2 (Sec. III.C),
+ * eps = 0, max_iter = 10 (Sec. IV.C), FP64, fixed iterations. */
+void histretinex_default_params(hr_params* p);
+
+/* Creates a context on `device` for parameters *p (copied).  Builds the per-K tables
+ * (the Eq. 19 class map as per-row class boundaries).  Returns HR_ERR_INVALID_ARG for
+ * invalid parameters, HR_ERR_CUDA / HR_ERR_OOM on device failures. */
+hr_status histretinex_create(hr_ctx** out, const hr_params* p, int device);
+
+/* Enhances one image already in device memory (Sec. III, the whole pipeline above).
+ * d_in, d_out: device pointers to W x H interleaved RGB images (may alias);
+ * in_pitch, out_pitch: row strides in bytes; elem_bytes: 1 or 2.
+ * Asynchronous on `stream`; the context's workspace is reused by the next call on any
+ * stream, so calls on one context must be ordered (same stream or synchronised).
+ * Images with W*H >= 2^31 return HR_ERR_UNSUPPORTED. */
+hr_status histretinex_enhance(hr_ctx* ctx, const void* d_in, void* d_out, int width, int height,
+                              size_t in_pitch, size_t out_pitch, int elem_bytes, void* stream);
+
+/* Enhances n images (each as in histretinex_enhance) with one launch per pipeline stage:
+ * persistent kernels walk per-image work queues, so images of mixed sizes share the GPU.
+ * The arrays are HOST arrays of length n (d_in[i], d_out[i] are device pointers).
+ * Each image's result is identical to what histretinex_enhance returns for it alone. */
+hr_status histretinex_enhance_batch(hr_ctx* ctx, int n, const void* const* d_in, void* const* d_out,
+                                    const int* width, const int* height, const size_t* in_pitch,
+                                    const size_t* out_pitch, int elem_bytes, void* stream);
+
+/* End-to-end form: copies a HOST image to the device, enhances it, copies the result back
+ * into a HOST buffer and waits for the stream.  Pinned host memory gives full copy speed. */
+hr_status histretinex_enhance_host(hr_ctx* ctx, const void* h_in, void* h_out, int width, int height,
+                                   size_t in_pitch, size_t out_pitch, int elem_bytes, void* stream);
+
+/* Intermediates of image `image` of the last enhance / enhance_batch call (index 0 for
+ * enhance).  Needs HR_FLAG_DEBUG_OUT.  All outputs are HOST arrays of K entries (any may
+ * be NULL): S = H_C(S), G = H_C(grad S), R = H_C(R), L = H_C(L) after Algorithm 1,
+ * T = the enhanced histogram of Eq. 20, lut = the matching LUT; *iters = iterations run.
+ * Synchronises the device. */
+hr_status histretinex_get_debug(hr_ctx* ctx, int image, uint64_t* S, uint64_t* G, double* R, double* L,
+                                double* T, uint16_t* lut, int* iters);
+
+/* Waits for `stream` and returns the device status of the calls issued so far (HR_OK,
+ * HR_ERR_RANGE or HR_ERR_TIMEOUT), then clears it. */
+hr_status histretinex_sync_status(hr_ctx* ctx, void* stream);
+
+/* Frees the context and everything it owns.  NULL is accepted. */
+hr_status histretinex_destroy(hr_ctx* ctx);
+
+/* Static description of a status code. */
+const char* histretinex_status_string(hr_status s);
+
+/* Stage timing (needs HR_FLAG_STAGE_TIMING): every enhance / enhance_batch call records CUDA
+ * events on its own stream before and after each of its three stages.  This call waits for
+ * them and writes the summed device times in milliseconds since the last reset to ms[0]
+ * (histogram pass), ms[1] (solve: Algorithm 1, Eq. 20, LUT) and ms[2] (apply pass), and the
+ * number of calls covered to *calls; reset != 0 clears the sums afterwards.  Not part of the
+ * paper's method: a measurement hook. */
+hr_status histretinex_stage_times(hr_ctx* ctx, double* ms, int* calls, int reset);
+
+/* Number of kernels this library launched on the context since creation (for
+ * launch accounting by callers and benchmarks). */
+uint64_t histretinex_kernel_launches(const hr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HISTRETINEX_H */

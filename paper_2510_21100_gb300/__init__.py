@@ -1,0 +1,250 @@
+"""HistRetinex on GB300: Python binding of the C-ABI library ``libhistretinex.so``.
+
+Argument marshalling only: every step of the pipeline runs in the library's CUDA kernels.
+PyTorch tensors provide device memory and streams; only raw pointers, sizes and a
+cudaStream_t cross the C ABI (``include/histretinex.h``).  The binding refuses to run
+without the compiled library: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libhistretinex.so")
+
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_RANGE, ERR_TIMEOUT = range(7)
+PREC_FP64, PREC_FP32 = 0, 1
+FLAG_FIXED_ITERS, FLAG_DEBUG_OUT, FLAG_STAGE_TIMING = 1, 2, 4
+
+# Every symbol include/histretinex.h declares.
+EXPORTS = (
+    "histretinex_default_params", "histretinex_create", "histretinex_enhance", "histretinex_enhance_batch",
+    "histretinex_enhance_host", "histretinex_get_debug", "histretinex_sync_status", "histretinex_destroy",
+    "histretinex_status_string", "histretinex_kernel_launches", "histretinex_stage_times",
+)
+
+
+class hr_params(ctypes.Structure):
+    _fields_ = [
+        ("K", ctypes.c_int),
+        ("alpha", ctypes.c_double),
+        ("beta", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+        ("eps", ctypes.c_double),
+        ("max_iter", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("flags", ctypes.c_uint),
+    ]
+
+
+class HistRetinexError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        msg = _lib().histretinex_status_string(code).decode() if _LIB is not None else str(code)
+        super().__init__(f"{what}: {msg} (status {code})" if what else f"{msg} (status {code})")
+        self.code = code
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build the CUDA library first "
+                "(python -m paper_2510_21100_gb300.build); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, sz, u = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_uint
+        L.histretinex_default_params.argtypes = [ctypes.POINTER(hr_params)]
+        L.histretinex_default_params.restype = None
+        L.histretinex_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(hr_params), i]
+        L.histretinex_enhance.argtypes = [vp, vp, vp, i, i, sz, sz, i, vp]
+        L.histretinex_enhance_batch.argtypes = [vp, i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i),
+                                                ctypes.POINTER(i), ctypes.POINTER(sz), ctypes.POINTER(sz), i, vp]
+        L.histretinex_enhance_host.argtypes = [vp, vp, vp, i, i, sz, sz, i, vp]
+        L.histretinex_get_debug.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, ctypes.POINTER(i)]
+        L.histretinex_sync_status.argtypes = [vp, vp]
+        L.histretinex_destroy.argtypes = [vp]
+        L.histretinex_status_string.argtypes = [i]
+        L.histretinex_status_string.restype = ctypes.c_char_p
+        L.histretinex_kernel_launches.argtypes = [vp]
+        L.histretinex_kernel_launches.restype = ctypes.c_uint64
+        L.histretinex_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i), i]
+        L.histretinex_stage_times.restype = ctypes.c_int
+        for name in ("histretinex_create", "histretinex_enhance", "histretinex_enhance_batch",
+                     "histretinex_enhance_host", "histretinex_get_debug", "histretinex_sync_status",
+                     "histretinex_destroy"):
+            getattr(L, name).restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def library():
+    """The loaded ctypes library (raises if it has not been built)."""
+    return _lib()
+
+
+@dataclass
+class Params:
+    """Method parameters (see hr_params in include/histretinex.h)."""
+    K: int = 256
+    alpha: float = 1e-3
+    beta: float = 1e-3
+    gamma: float = 2.2
+    eps: float = 0.0
+    max_iter: int = 10
+    precision: int = PREC_FP64
+    fixed_iters: bool = True
+    debug: bool = False
+    stage_timing: bool = False
+
+    def c(self) -> hr_params:
+        flags = (FLAG_FIXED_ITERS if self.fixed_iters else 0) | (FLAG_DEBUG_OUT if self.debug else 0) | \
+            (FLAG_STAGE_TIMING if self.stage_timing else 0)
+        return hr_params(self.K, self.alpha, self.beta, self.gamma, self.eps, self.max_iter, self.precision, flags)
+
+
+def _check(code, what=""):
+    if code != OK:
+        raise HistRetinexError(code, what)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _geom(t):
+    """(W, H, pitch_bytes, elem_bytes) of an (H, W, 3) uint8/uint16 tensor with unit channel stride."""
+    import torch
+    if t.dim() != 3 or t.shape[2] != 3 or t.dtype not in (torch.uint8, torch.uint16):
+        raise ValueError("images are (H, W, 3) uint8 or uint16 tensors")
+    eb = t.element_size()
+    if t.stride(2) != 1 or t.stride(1) != 3:
+        raise ValueError("pixels must be interleaved RGB (channel stride 1, pixel stride 3)")
+    return int(t.shape[1]), int(t.shape[0]), int(t.stride(0)) * eb, eb
+
+
+class Context:
+    """A HistRetinex context on one CUDA device (owns workspace and per-K tables)."""
+
+    def __init__(self, params: Params | None = None, device: int = 0):
+        self.params = params or Params()
+        self._h = ctypes.c_void_p()
+        cp = self.params.c()
+        _check(_lib().histretinex_create(ctypes.byref(self._h), ctypes.byref(cp), device), "histretinex_create")
+        self.device = device
+
+    def close(self):
+        if self._h:
+            _lib().histretinex_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def enhance(self, d_in, d_out=None, stream=None):
+        """Enhance one device image (torch tensor (H, W, 3) uint8/uint16); d_out may be d_in."""
+        if d_out is None:
+            import torch
+            d_out = torch.empty_like(d_in)
+        W, H, pin, eb = _geom(d_in)
+        W2, H2, pout, eb2 = _geom(d_out)
+        if (W, H, eb) != (W2, H2, eb2):
+            raise ValueError("input and output images differ in shape or type")
+        _check(_lib().histretinex_enhance(self._h, ctypes.c_void_p(d_in.data_ptr()), ctypes.c_void_p(d_out.data_ptr()),
+                                          W, H, pin, pout, eb, _stream_ptr(stream)), "histretinex_enhance")
+        return d_out
+
+    def enhance_ptr(self, in_ptr: int, out_ptr: int, W: int, H: int, in_pitch: int, out_pitch: int, elem_bytes: int,
+                    stream=None):
+        _check(_lib().histretinex_enhance(self._h, ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), W, H, in_pitch,
+                                          out_pitch, elem_bytes, _stream_ptr(stream)), "histretinex_enhance")
+
+    def enhance_batch(self, ins, outs=None, stream=None):
+        """Enhance a list of device images with one launch per pipeline stage."""
+        import torch
+        if outs is None:
+            outs = [torch.empty_like(t) for t in ins]
+        n = len(ins)
+        if n != len(outs) or n == 0:
+            raise ValueError("need matching, non-empty input and output lists")
+        g = [_geom(t) for t in ins]
+        go = [_geom(t) for t in outs]
+        eb = g[0][3]
+        if any(x[3] != eb for x in g + go) or any(a[:2] != b[:2] for a, b in zip(g, go)):
+            raise ValueError("all images must share one element type and outputs must match inputs")
+        VP = ctypes.c_void_p * n
+        I = ctypes.c_int * n
+        SZ = ctypes.c_size_t * n
+        _check(_lib().histretinex_enhance_batch(
+            self._h, n, VP(*[t.data_ptr() for t in ins]), VP(*[t.data_ptr() for t in outs]), I(*[x[0] for x in g]),
+            I(*[x[1] for x in g]), SZ(*[x[2] for x in g]), SZ(*[x[2] for x in go]), eb, _stream_ptr(stream)),
+            "histretinex_enhance_batch")
+        return outs
+
+    def enhance_host(self, h_in, h_out=None, stream=None):
+        """End to end from host memory: numpy arrays or (pinned) CPU tensors, (H, W, 3) uint8/uint16."""
+        import numpy as np
+        if h_out is None:
+            h_out = np.empty_like(h_in) if isinstance(h_in, np.ndarray) else h_in.new_empty(h_in.shape)
+        if isinstance(h_in, np.ndarray):
+            H, W, _ = h_in.shape
+            eb = h_in.dtype.itemsize
+            pin, pout = h_in.strides[0], h_out.strides[0]
+            pi, po = h_in.ctypes.data, h_out.ctypes.data
+        else:
+            W, H, pin, eb = _geom(h_in)
+            _, _, pout, _ = _geom(h_out)
+            pi, po = h_in.data_ptr(), h_out.data_ptr()
+        _check(_lib().histretinex_enhance_host(self._h, ctypes.c_void_p(pi), ctypes.c_void_p(po), W, H, pin, pout, eb,
+                                               _stream_ptr(stream)), "histretinex_enhance_host")
+        return h_out
+
+    def sync_status(self, stream=None):
+        return _lib().histretinex_sync_status(self._h, _stream_ptr(stream))
+
+    def check(self, stream=None):
+        _check(self.sync_status(stream), "device status")
+
+    def debug(self, image: int = 0):
+        """Intermediates of the last call (needs Params(debug=True)): dict of numpy arrays."""
+        import numpy as np
+        K = self.params.K
+        S = np.zeros(K, np.uint64)
+        G = np.zeros(K, np.uint64)
+        R = np.zeros(K, np.float64)
+        L = np.zeros(K, np.float64)
+        T = np.zeros(K, np.float64)
+        lut = np.zeros(K, np.uint16)
+        it = ctypes.c_int(0)
+        p = lambda a: ctypes.c_void_p(a.ctypes.data)
+        _check(_lib().histretinex_get_debug(self._h, image, p(S), p(G), p(R), p(L), p(T), p(lut), ctypes.byref(it)),
+               "histretinex_get_debug")
+        return dict(S=S, G=G, R=R, L=L, T=T, lut=lut, iters=it.value)
+
+    def stage_times(self, reset: bool = False):
+        """(hist_ms, solve_ms, apply_ms, calls) summed since the last reset (needs stage_timing=True)."""
+        ms = (ctypes.c_double * 3)()
+        calls = ctypes.c_int(0)
+        _check(_lib().histretinex_stage_times(self._h, ms, ctypes.byref(calls), int(reset)), "histretinex_stage_times")
+        return ms[0], ms[1], ms[2], calls.value
+
+    def kernel_launches(self) -> int:
+        return int(_lib().histretinex_kernel_launches(self._h))

@@ -1,0 +1,452 @@
+// C ABI of the HistRetinex CUDA library: context, workspace, per-K tables, launches.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/histretinex.h"
+#include "hr_internal.cuh"
+
+using hr::ImageDesc;
+using hr::SlotLayout;
+
+struct hr_ctx {
+  int device = 0;
+  hr_params p{};
+  SlotLayout lay{};
+  int sm_count = 0;
+  uint8_t* d_slots = nullptr;
+  int n_slots = 0;
+  uint16_t* d_jstart1 = nullptr;   // [K][K+1], index_1 class boundaries (Eq. 19)
+  unsigned* d_status = nullptr;
+  ImageDesc* d_imgs = nullptr;
+  int* d_tile_start = nullptr;
+  int cap_imgs = 0;
+  ImageDesc* h_imgs = nullptr;     // pinned staging for the descriptors
+  int* h_tile_start = nullptr;
+  cudaEvent_t desc_done = nullptr; // the last descriptor upload has been consumed
+  std::vector<ImageDesc> last_imgs;
+  void* d_io_in = nullptr;         // device copies for the host-buffer entry point
+  void* d_io_out = nullptr;
+  size_t io_bytes = 0;
+  uint64_t launches = 0;
+  int last_n = 0;
+  // stage timing: a ring of event quadruples, folded into the sums when reused or queried
+  static constexpr int kRing = 256;
+  cudaEvent_t ev[kRing][4] = {};
+  bool ev_used[kRing] = {};
+  int ev_next = 0;
+  double stage_ms[3] = {0, 0, 0};
+  int stage_calls = 0;
+};
+
+namespace hr {
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+SlotLayout make_layout(int K) {
+  SlotLayout L{};
+  size_t o = 0;
+  L.S = o; o += (size_t)K * 4;
+  L.G = o; o += (size_t)K * 4;
+  o = align256(o);
+  L.R = o; o += (size_t)K * 8;
+  L.L = o; o += (size_t)K * 8;
+  L.T = o; o += (size_t)K * 8;
+  L.lut = o; o += (size_t)K * 2;
+  o = align256(o);
+  L.misc = o; o += 16;
+  o = align256(o);
+  L.vec = o; o += (K > 1024) ? (size_t)kSolveVecs * K * 8 : 0;
+  o = align256(o);
+  L.cls = o; o += (size_t)4 * K * 4;
+  o = align256(o);
+  L.list = o; o += (size_t)K * K * 4;
+  o = align256(o);
+  L.max_pieces = (size_t)K * K / kPiece + K;
+  L.piece = o; o += L.max_pieces * 8;
+  o = align256(o);
+  size_t mp = L.max_pieces;
+  const size_t dense = (size_t)K * ((K + kPiece - 1) / kPiece);
+  if (dense > mp) mp = dense;
+  if (mp < (size_t)kSolveThreads) mp = kSolveThreads;
+  L.max_parts = mp;
+  L.part = o; o += mp * 8;
+  L.bytes = align256(o);
+  return L;
+}
+
+}  // namespace hr
+
+namespace {
+
+hr_status cuda_fail(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) return HR_ERR_OOM;
+  return e == cudaSuccess ? HR_OK : HR_ERR_CUDA;
+}
+
+#define HR_CUDA(x)                                 \
+  do {                                             \
+    cudaError_t e_ = (x);                          \
+    if (e_ != cudaSuccess) return cuda_fail(e_);   \
+  } while (0)
+
+bool pow2(int k) { return k > 0 && (k & (k - 1)) == 0; }
+
+hr_status check_params(const hr_params* p) {
+  if (!p) return HR_ERR_INVALID_ARG;
+  if (!pow2(p->K) || p->K < 8 || p->K > 4096) return HR_ERR_INVALID_ARG;
+  if (!(p->alpha > 0.0) || !(p->beta > 0.0) || !(p->gamma > 0.0) || !(p->eps >= 0.0)) return HR_ERR_INVALID_ARG;
+  if (!std::isfinite(p->alpha) || !std::isfinite(p->beta) || !std::isfinite(p->gamma)) return HR_ERR_INVALID_ARG;
+  if (p->max_iter < 1) return HR_ERR_INVALID_ARG;
+  if (p->precision != HR_PREC_FP64 && p->precision != HR_PREC_FP32) return HR_ERR_INVALID_ARG;
+  return HR_OK;
+}
+
+// index_1(i, j) (Eq. 17-19): the level whose location k/(K-1) is nearest to the gamma-processed
+// location matrix entry (j/(K-1))^(1/gamma) * i/(K-1); the first such level on a tie.  The
+// distance is unimodal in k, so the minimum lies next to the rounded position.
+int index1(int K, double hl, double hr) {
+  const double km1 = (double)(K - 1);
+  const double p = hl * hr;
+  long c = std::lround(p * km1);
+  long lo = c - 1 < 0 ? 0 : c - 1, hi = c + 1 > K - 1 ? K - 1 : c + 1;
+  long best = lo;
+  double bd = std::fabs(p - (double)lo / km1);
+  for (long k = lo + 1; k <= hi; ++k) {
+    const double d = std::fabs(p - (double)k / km1);
+    if (d < bd) { bd = d; best = k; }
+  }
+  return (int)best;
+}
+
+// jstart1[i][k] = first illumination bin j with index_1(i, j) >= k (index_1 grows with j).
+void build_jstart1(int K, double gamma, std::vector<uint16_t>& t) {
+  t.assign((size_t)K * (K + 1), 0);
+  const double km1 = (double)(K - 1);
+  const double ig = 1.0 / gamma;
+  std::vector<double> hl(K);
+  for (int j = 0; j < K; ++j) hl[j] = std::pow((double)j / km1, ig);
+  for (int i = 0; i < K; ++i) {
+    const double hr = (double)i / km1;
+    uint16_t* row = t.data() + (size_t)i * (K + 1);
+    int k = 0;
+    for (int j = 0; j < K; ++j) {
+      const int c = index1(K, hl[j], hr);
+      while (k <= c) row[k++] = (uint16_t)j;
+    }
+    while (k <= K) row[k++] = (uint16_t)K;
+  }
+}
+
+hr_status ensure_slots(hr_ctx* c, int n) {
+  if (n <= c->n_slots) return HR_OK;
+  if (c->d_slots) { cudaFree(c->d_slots); c->d_slots = nullptr; c->n_slots = 0; }
+  HR_CUDA(cudaMalloc(&c->d_slots, c->lay.bytes * (size_t)n));
+  c->n_slots = n;
+  return HR_OK;
+}
+
+hr_status ensure_desc(hr_ctx* c, int n) {
+  if (n <= c->cap_imgs) return HR_OK;
+  if (c->desc_done) HR_CUDA(cudaEventSynchronize(c->desc_done));
+  cudaFree(c->d_imgs); cudaFree(c->d_tile_start); cudaFreeHost(c->h_imgs); cudaFreeHost(c->h_tile_start);
+  c->d_imgs = nullptr; c->d_tile_start = nullptr; c->h_imgs = nullptr; c->h_tile_start = nullptr; c->cap_imgs = 0;
+  c->last_imgs.clear();
+  HR_CUDA(cudaMalloc(&c->d_imgs, sizeof(ImageDesc) * (size_t)n));
+  HR_CUDA(cudaMalloc(&c->d_tile_start, sizeof(int) * (size_t)(n + 1)));
+  HR_CUDA(cudaMallocHost(&c->h_imgs, sizeof(ImageDesc) * (size_t)n));
+  HR_CUDA(cudaMallocHost(&c->h_tile_start, sizeof(int) * (size_t)(n + 1)));
+  c->cap_imgs = n;
+  return HR_OK;
+}
+
+bool same_desc(const std::vector<ImageDesc>& a, const ImageDesc* b, int n) {
+  if ((int)a.size() != n) return false;
+  for (int i = 0; i < n; ++i)
+    if (a[i].in != b[i].in || a[i].out != b[i].out || a[i].W != b[i].W || a[i].H != b[i].H ||
+        a[i].in_pitch != b[i].in_pitch || a[i].out_pitch != b[i].out_pitch)
+      return false;
+  return true;
+}
+
+// Adds the stage times of ring entry i to the sums (waits for its last event).
+hr_status fold_timing(hr_ctx* c, int i) {
+  if (!c->ev_used[i]) return HR_OK;
+  HR_CUDA(cudaEventSynchronize(c->ev[i][3]));
+  for (int s = 0; s < 3; ++s) {
+    float ms = 0.f;
+    HR_CUDA(cudaEventElapsedTime(&ms, c->ev[i][s], c->ev[i][s + 1]));
+    c->stage_ms[s] += ms;
+  }
+  c->stage_calls += 1;
+  c->ev_used[i] = false;
+  return HR_OK;
+}
+
+hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, cudaStream_t st) {
+  const int K = c->p.K;
+  if (elem_bytes != 1 && elem_bytes != 2) return HR_ERR_INVALID_ARG;
+  if (elem_bytes == 1 && K > 256) return HR_ERR_INVALID_ARG;
+  if (c->p.precision != HR_PREC_FP64) return HR_ERR_UNSUPPORTED;
+  long long total = 0;
+  for (int i = 0; i < n; ++i) {
+    const ImageDesc& d = imgs[i];
+    if (!d.in || !d.out || d.W < 1 || d.H < 1) return HR_ERR_INVALID_ARG;
+    if ((long long)d.in_pitch < 3LL * d.W * elem_bytes || (long long)d.out_pitch < 3LL * d.W * elem_bytes)
+      return HR_ERR_INVALID_ARG;
+    if ((long long)d.W * d.H >= (1LL << 31)) return HR_ERR_UNSUPPORTED;
+    total += hr::tiles_of(d.W, d.H);
+  }
+  if (total >= (1LL << 31)) return HR_ERR_UNSUPPORTED;
+  hr_status s = ensure_slots(c, n);
+  if (s != HR_OK) return s;
+  s = ensure_desc(c, n);
+  if (s != HR_OK) return s;
+  if (!same_desc(c->last_imgs, imgs, n)) {
+    HR_CUDA(cudaEventSynchronize(c->desc_done));  // the previous upload has left the staging buffer
+    int t = 0;
+    for (int i = 0; i < n; ++i) {
+      c->h_imgs[i] = imgs[i];
+      c->h_tile_start[i] = t;
+      t += hr::tiles_of(imgs[i].W, imgs[i].H);
+    }
+    c->h_tile_start[n] = t;
+    HR_CUDA(cudaMemcpyAsync(c->d_imgs, c->h_imgs, sizeof(ImageDesc) * (size_t)n, cudaMemcpyHostToDevice, st));
+    HR_CUDA(cudaMemcpyAsync(c->d_tile_start, c->h_tile_start, sizeof(int) * (size_t)(n + 1), cudaMemcpyHostToDevice,
+                            st));
+    HR_CUDA(cudaEventRecord(c->desc_done, st));
+    c->last_imgs.assign(imgs, imgs + n);
+  }
+  // zero H_C(S) and H_C(grad S) of every slot used (S and G are adjacent at the slot start)
+  HR_CUDA(cudaMemset2DAsync(c->d_slots + c->lay.S, c->lay.bytes, 0, (size_t)2 * K * sizeof(unsigned), (size_t)n, st));
+  const int px_grid = c->sm_count * 8;
+  const bool timing = (c->p.flags & HR_FLAG_STAGE_TIMING) != 0;
+  cudaEvent_t* ev = nullptr;
+  if (timing) {
+    const int i = c->ev_next;
+    c->ev_next = (i + 1) % hr_ctx::kRing;
+    hr_status fs = fold_timing(c, i);
+    if (fs != HR_OK) return fs;
+    if (!c->ev[i][0])
+      for (int q = 0; q < 4; ++q) HR_CUDA(cudaEventCreate(&c->ev[i][q]));
+    ev = c->ev[i];
+    c->ev_used[i] = true;
+    HR_CUDA(cudaEventRecord(ev[0], st));
+  }
+  HR_CUDA(hr::launch_hist(c->d_imgs, n, c->d_tile_start, (int)total, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay,
+                          c->d_status, px_grid, st));
+  if (ev) HR_CUDA(cudaEventRecord(ev[1], st));
+  hr::SolveArgs a{};
+  a.K = K;
+  a.alpha = c->p.alpha;
+  a.beta = c->p.beta;
+  a.eps = c->p.eps;
+  a.max_iter = c->p.max_iter;
+  a.fixed_iters = (c->p.flags & HR_FLAG_FIXED_ITERS) ? 1 : 0;
+  a.jstart1 = c->d_jstart1;
+  a.slots = c->d_slots;
+  a.slot_bytes = c->lay.bytes;
+  a.lay = c->lay;
+  a.status = c->d_status;
+  a.vec_in_smem = K <= 1024 ? 1 : 0;
+  HR_CUDA(hr::launch_solve(a, n, st));
+  if (ev) HR_CUDA(cudaEventRecord(ev[2], st));
+  HR_CUDA(hr::launch_apply(c->d_imgs, n, c->d_tile_start, (int)total, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay,
+                           c->d_status, px_grid, st));
+  if (ev) HR_CUDA(cudaEventRecord(ev[3], st));
+  c->launches += 3;
+  c->last_n = n;
+  return HR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void histretinex_default_params(hr_params* p) {
+  if (!p) return;
+  p->K = 256;
+  p->alpha = 1e-3;
+  p->beta = 1e-3;
+  p->gamma = 2.2;
+  p->eps = 0.0;
+  p->max_iter = 10;
+  p->precision = HR_PREC_FP64;
+  p->flags = HR_FLAG_FIXED_ITERS;
+}
+
+hr_status histretinex_create(hr_ctx** out, const hr_params* p, int device) {
+  if (!out) return HR_ERR_INVALID_ARG;
+  *out = nullptr;
+  hr_status s = check_params(p);
+  if (s != HR_OK) return s;
+  int ndev = 0;
+  HR_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return HR_ERR_INVALID_ARG;
+  HR_CUDA(cudaSetDevice(device));
+  hr_ctx* c = new (std::nothrow) hr_ctx();
+  if (!c) return HR_ERR_OOM;
+  c->device = device;
+  c->p = *p;
+  c->lay = hr::make_layout(p->K);
+  cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  std::vector<uint16_t> js;
+  build_jstart1(p->K, p->gamma, js);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_jstart1, js.size() * sizeof(uint16_t));
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_jstart1, js.data(), js.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->desc_done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    histretinex_destroy(c);
+    return cuda_fail(e);
+  }
+  *out = c;
+  return HR_OK;
+}
+
+hr_status histretinex_enhance(hr_ctx* c, const void* d_in, void* d_out, int width, int height, size_t in_pitch,
+                              size_t out_pitch, int elem_bytes, void* stream) {
+  if (!c) return HR_ERR_INVALID_ARG;
+  ImageDesc d{static_cast<const uint8_t*>(d_in), static_cast<uint8_t*>(d_out), width, height, (long long)in_pitch,
+              (long long)out_pitch};
+  HR_CUDA(cudaSetDevice(c->device));
+  return run_pipeline(c, 1, &d, elem_bytes, static_cast<cudaStream_t>(stream));
+}
+
+hr_status histretinex_enhance_batch(hr_ctx* c, int n, const void* const* d_in, void* const* d_out, const int* width,
+                                    const int* height, const size_t* in_pitch, const size_t* out_pitch,
+                                    int elem_bytes, void* stream) {
+  if (!c || n < 1 || !d_in || !d_out || !width || !height || !in_pitch || !out_pitch) return HR_ERR_INVALID_ARG;
+  std::vector<ImageDesc> v((size_t)n);
+  for (int i = 0; i < n; ++i)
+    v[i] = ImageDesc{static_cast<const uint8_t*>(d_in[i]), static_cast<uint8_t*>(d_out[i]), width[i], height[i],
+                     (long long)in_pitch[i], (long long)out_pitch[i]};
+  HR_CUDA(cudaSetDevice(c->device));
+  return run_pipeline(c, n, v.data(), elem_bytes, static_cast<cudaStream_t>(stream));
+}
+
+hr_status histretinex_enhance_host(hr_ctx* c, const void* h_in, void* h_out, int width, int height, size_t in_pitch,
+                                   size_t out_pitch, int elem_bytes, void* stream) {
+  if (!c || !h_in || !h_out || width < 1 || height < 1 || (elem_bytes != 1 && elem_bytes != 2))
+    return HR_ERR_INVALID_ARG;
+  const size_t row = (size_t)3 * width * elem_bytes;
+  if (in_pitch < row || out_pitch < row) return HR_ERR_INVALID_ARG;
+  const size_t bytes = row * (size_t)height;
+  HR_CUDA(cudaSetDevice(c->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (bytes > c->io_bytes) {
+    HR_CUDA(cudaStreamSynchronize(st));
+    cudaFree(c->d_io_in); cudaFree(c->d_io_out);
+    c->d_io_in = c->d_io_out = nullptr; c->io_bytes = 0;
+    HR_CUDA(cudaMalloc(&c->d_io_in, bytes));
+    HR_CUDA(cudaMalloc(&c->d_io_out, bytes));
+    c->io_bytes = bytes;
+  }
+  HR_CUDA(cudaMemcpy2DAsync(c->d_io_in, row, h_in, in_pitch, row, (size_t)height, cudaMemcpyHostToDevice, st));
+  ImageDesc d{static_cast<const uint8_t*>(c->d_io_in), static_cast<uint8_t*>(c->d_io_out), width, height,
+              (long long)row, (long long)row};
+  hr_status s = run_pipeline(c, 1, &d, elem_bytes, st);
+  if (s != HR_OK) return s;
+  HR_CUDA(cudaMemcpy2DAsync(h_out, out_pitch, c->d_io_out, row, row, (size_t)height, cudaMemcpyDeviceToHost, st));
+  return histretinex_sync_status(c, stream);
+}
+
+hr_status histretinex_get_debug(hr_ctx* c, int image, uint64_t* S, uint64_t* G, double* R, double* L, double* T,
+                                uint16_t* lut, int* iters) {
+  if (!c || image < 0 || image >= c->last_n) return HR_ERR_INVALID_ARG;
+  if (!(c->p.flags & HR_FLAG_DEBUG_OUT)) return HR_ERR_INVALID_ARG;
+  HR_CUDA(cudaSetDevice(c->device));
+  HR_CUDA(cudaDeviceSynchronize());
+  const int K = c->p.K;
+  const uint8_t* slot = c->d_slots + (size_t)image * c->lay.bytes;
+  std::vector<unsigned> tmp((size_t)K);
+  if (S) {
+    HR_CUDA(cudaMemcpy(tmp.data(), slot + c->lay.S, (size_t)K * 4, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < K; ++k) S[k] = tmp[k];
+  }
+  if (G) {
+    HR_CUDA(cudaMemcpy(tmp.data(), slot + c->lay.G, (size_t)K * 4, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < K; ++k) G[k] = tmp[k];
+  }
+  if (R) HR_CUDA(cudaMemcpy(R, slot + c->lay.R, (size_t)K * 8, cudaMemcpyDeviceToHost));
+  if (L) HR_CUDA(cudaMemcpy(L, slot + c->lay.L, (size_t)K * 8, cudaMemcpyDeviceToHost));
+  if (T) HR_CUDA(cudaMemcpy(T, slot + c->lay.T, (size_t)K * 8, cudaMemcpyDeviceToHost));
+  if (lut) HR_CUDA(cudaMemcpy(lut, slot + c->lay.lut, (size_t)K * 2, cudaMemcpyDeviceToHost));
+  if (iters) {
+    int m[4];
+    HR_CUDA(cudaMemcpy(m, slot + c->lay.misc, sizeof(m), cudaMemcpyDeviceToHost));
+    *iters = m[0];
+  }
+  return HR_OK;
+}
+
+hr_status histretinex_sync_status(hr_ctx* c, void* stream) {
+  if (!c) return HR_ERR_INVALID_ARG;
+  HR_CUDA(cudaSetDevice(c->device));
+  HR_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  unsigned st = 0;
+  HR_CUDA(cudaMemcpy(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  HR_CUDA(cudaMemset(c->d_status, 0, sizeof(unsigned)));
+  if (st & hr::kStTimeout) return HR_ERR_TIMEOUT;
+  if (st & hr::kStRange) return HR_ERR_RANGE;
+  if (st & hr::kStUnsupported) return HR_ERR_UNSUPPORTED;
+  return HR_OK;
+}
+
+hr_status histretinex_destroy(hr_ctx* c) {
+  if (!c) return HR_OK;
+  cudaSetDevice(c->device);
+  if (c->desc_done) cudaEventSynchronize(c->desc_done);
+  cudaFree(c->d_slots);
+  cudaFree(c->d_jstart1);
+  cudaFree(c->d_status);
+  cudaFree(c->d_imgs);
+  cudaFree(c->d_tile_start);
+  cudaFreeHost(c->h_imgs);
+  cudaFreeHost(c->h_tile_start);
+  cudaFree(c->d_io_in);
+  cudaFree(c->d_io_out);
+  if (c->desc_done) cudaEventDestroy(c->desc_done);
+  for (int i = 0; i < hr_ctx::kRing; ++i)
+    for (int q = 0; q < 4; ++q)
+      if (c->ev[i][q]) cudaEventDestroy(c->ev[i][q]);
+  delete c;
+  return HR_OK;
+}
+
+const char* histretinex_status_string(hr_status s) {
+  switch (s) {
+    case HR_OK: return "ok";
+    case HR_ERR_INVALID_ARG: return "invalid argument";
+    case HR_ERR_UNSUPPORTED: return "unsupported request";
+    case HR_ERR_OOM: return "out of memory";
+    case HR_ERR_CUDA: return "CUDA runtime error";
+    case HR_ERR_RANGE: return "image level >= K";
+    case HR_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+hr_status histretinex_stage_times(hr_ctx* c, double* ms, int* calls, int reset) {
+  if (!c) return HR_ERR_INVALID_ARG;
+  HR_CUDA(cudaSetDevice(c->device));
+  for (int i = 0; i < hr_ctx::kRing; ++i) {
+    hr_status s = fold_timing(c, i);
+    if (s != HR_OK) return s;
+  }
+  if (ms)
+    for (int s = 0; s < 3; ++s) ms[s] = c->stage_ms[s];
+  if (calls) *calls = c->stage_calls;
+  if (reset) {
+    c->stage_ms[0] = c->stage_ms[1] = c->stage_ms[2] = 0.0;
+    c->stage_calls = 0;
+  }
+  return HR_OK;
+}
+
+uint64_t histretinex_kernel_launches(const hr_ctx* c) { return c ? c->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+// Internal declarations of the HistRetinex CUDA library (sm_103a).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hr {
+
+// Device status bits, OR-ed into the context's status word by the kernels.
+enum : unsigned { kStRange = 1u, kStTimeout = 2u, kStUnsupported = 4u };
+
+// Length of one accumulation piece of the solver (cells summed by one lane before the
+// per-target combine).  Short pieces keep the FP64 dependency chains short.
+constexpr int kPiece = 8;
+
+// One image of a launch: device pointers and geometry.
+struct ImageDesc {
+  const uint8_t* in;
+  uint8_t* out;
+  int W, H;
+  long long in_pitch, out_pitch;
+};
+
+// Byte offsets of the per-image workspace ("slot").  Every slot has the same layout for a
+// given K; slots are `slot_bytes` apart.
+struct SlotLayout {
+  size_t S, G;          // uint32[K] each: H_C(S), H_C(grad S)
+  size_t R, L, T;       // double[K] each: results of Algorithm 1 and Eq. 20 (level-indexed)
+  size_t lut;           // uint16[K]
+  size_t misc;          // int[4]: iterations, nR, nL, cells
+  size_t vec;           // solver vectors when they do not fit in shared memory
+  size_t cls;           // uint32[4*K]: class size, cell start, first piece, piece count
+  size_t list;          // uint32[K*K]: class-major cell list, (a << 16) | b
+  size_t piece;         // uint2[max_pieces]: (cell start, len | class << 16)
+  size_t part;          // double[max_parts]: piece partial sums
+  size_t bytes;         // total slot size (multiple of 256)
+  size_t max_pieces, max_parts;
+};
+
+SlotLayout make_layout(int K);
+
+// Number of solver vectors (double[K]) and their shared-memory footprint.
+constexpr int kSolveVecs = 8;       // Rc, Lc, L2c, RRc, Ru, Lu, q, spare
+constexpr int kSolveThreads = 512;
+
+struct SolveArgs {
+  int K;
+  double alpha, beta, eps;
+  int max_iter;
+  int fixed_iters;
+  const uint16_t* jstart1;   // [K][K+1]: first illumination bin j with index_1(i, j) >= k
+  uint8_t* slots;            // base of slot 0
+  size_t slot_bytes;
+  SlotLayout lay;
+  unsigned* status;
+  int vec_in_smem;           // 1: solver vectors in dynamic shared memory
+};
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_hist(const ImageDesc* d_imgs, int n, const int* d_tile_start, int total_tiles, int elem_bytes,
+                        int K, uint8_t* slots, size_t slot_bytes, SlotLayout lay, unsigned* status,
+                        int grid, cudaStream_t st);
+cudaError_t launch_solve(const SolveArgs& a, int n, cudaStream_t st);
+cudaError_t launch_apply(const ImageDesc* d_imgs, int n, const int* d_tile_start, int total_tiles, int elem_bytes,
+                         int K, uint8_t* slots, size_t slot_bytes, SlotLayout lay, unsigned* status, int grid,
+                         cudaStream_t st);
+size_t solve_smem_bytes(int K, int vec_in_smem);
+
+// Geometry of the pixel passes: tiles of kTileW x kTileH pixels.
+constexpr int kTileW = 128;
+constexpr int kTileH = 32;
+inline int tiles_of(int W, int H) { return ((W + kTileW - 1) / kTileW) * ((H + kTileH - 1) / kTileH); }
+
+}  // namespace hr
