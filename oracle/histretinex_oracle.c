@@ -317,7 +317,10 @@ int orc_target(const double* R, const double* L, int K, double gamma, uint64_t N
 /* ---------- Stage 5: histogram matching (Sec. III.C, last paragraph) ---------- */
 
 /* LUT[s] = smallest z with CT(z) * N >= CS(s) * TT, where CS is the integer cumulative
- * count of S, CT the cumulative sum of the target (ascending), TT = CT(K-1); K-1 if none. */
+ * count of S, CT the cumulative sum of the target (ascending), TT = CT(K-1); K-1 if none.
+ * Where CS(s) = N the condition is CT(z) >= TT, which in exact arithmetic holds from the last
+ * occupied target level z_top on; that level is used directly, because a running FP64 sum
+ * can absorb trailing bins far below its ulp and reach TT earlier. */
 int orc_lut(const uint64_t* S, const double* T, int K, uint16_t* lut) {
   if (K < 2 || K > 65536 || !S || !T || !lut) return ORC_ERR_INVALID_ARG;
   double* CT = (double*)malloc(sizeof(double) * (size_t)K);
@@ -328,9 +331,12 @@ int orc_lut(const uint64_t* S, const double* T, int K, uint16_t* lut) {
   uint64_t N = 0;
   for (int k = 0; k < K; ++k) N += S[k];
   const double Nd = (double)N;
+  int z_top = K - 1;
+  while (z_top > 0 && !(T[z_top] > 0.0)) --z_top;
   uint64_t cs = 0;
   for (int s = 0; s < K; ++s) {
     cs += S[s];
+    if (cs == N) { lut[s] = (uint16_t)z_top; continue; }
     const double rhs = (double)cs * TT;
     int z = 0;
     while (z < K - 1 && !(CT[z] * Nd >= rhs)) ++z;

@@ -401,12 +401,23 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     }
     const unsigned long long pm = tid > 0 ? tmax[tid - 1] : 0ull;
     for (int k = b0; k < b1; ++k) lhs[k] = lhs[k] > pm ? lhs[k] : pm;
+    // z_top: last occupied target level.  Where CS(s) = N the matching condition reads
+    // CT(z) >= TT, which in exact arithmetic first holds at z_top; that level is used directly.
+    int top_local = -1;
+    for (int k = b0; k < b1; ++k)
+      if (T[k] > 0.0) top_local = k;
+    unsigned* ztop = ured + NW + 1;
+    if (tid == 0) *ztop = 0u;
+    __syncthreads();
+    if (top_local >= 0) atomicMax(ztop, (unsigned)top_local);
     unsigned cs_local = 0;
     for (int k = b0; k < b1; ++k) cs_local += S[k];
     unsigned cs_total;
-    unsigned cs = block_exscan(cs_local, ured, &cs_total);
+    unsigned cs = block_exscan(cs_local, ured, &cs_total);  // (synchronises: ztop is final)
+    const int z_top = (int)*ztop;
     for (int k = b0; k < b1; ++k) {
       cs += S[k];
+      if (cs == Nu) { lut[k] = (uint16_t)z_top; continue; }
       const unsigned long long rhs = (unsigned long long)__double_as_longlong((double)cs * TT);
       int lo = 0, hi = K - 1;  // lhs[K-1] >= rhs unless no z qualifies; then K-1
       while (lo < hi) {

@@ -118,16 +118,20 @@ def target(R, L, K, gamma, N):
 
 
 def lut(S, T):
-    """Smallest z whose target CDF (scaled by N) reaches the source CDF (scaled by the target mass)."""
+    """Smallest z whose target CDF reaches the source CDF: CT(z) / CT(K-1) >= CS(s) / N, decided
+    in exact rational arithmetic over the given (double) target values."""
     K = len(S)
-    N = float(np.sum(S))
-    CT = np.cumsum(np.asarray(T, dtype=np.float64))
+    N = int(np.sum(S))
+    CT, acc = [], Fraction(0)
+    for t in T:
+        acc += Fraction(float(t))
+        CT.append(acc)
     TT = CT[-1]
     CS = np.cumsum(np.asarray(S, dtype=np.int64))
     out = np.zeros(K, dtype=np.int64)
     for s in range(K):
         z = 0
-        while z < K - 1 and not (CT[z] * N >= float(CS[s]) * TT):
+        while z < K - 1 and not (CT[z] * N >= int(CS[s]) * TT):
             z += 1
         out[s] = z
     return out

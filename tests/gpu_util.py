@@ -33,6 +33,8 @@ def ambiguous_lut_levels(S, T):
     lhs = CT * N
     amb = []
     for s in range(len(S)):
+        if CS[s] == N:  # top of the source CDF: decided exactly (last occupied target level)
+            continue
         rhs = CS[s] * TT
         if np.any(np.abs(lhs - rhs) <= LUT_MARGIN * max(abs(rhs), 1.0)):
             amb.append(s)

@@ -52,10 +52,39 @@ def test_gamma_moves_target_mass_to_brighter_levels():
     assert all(b > a for a, b in zip(means, means[1:]))
 
 
-def test_lut_matches_brute_force_search():
-    _, S, _, R, L = solved()
+def fp64_decision_margins(S, T):
+    """Per level s: relative distance of the FP64 comparison CT(z) N vs CS(s) TT from a tie, over all z."""
+    N = float(np.sum(S))
+    CT = np.cumsum(np.asarray(T, dtype=np.float64))
+    CS = np.cumsum(np.asarray(S, dtype=np.float64))
+    rhs = CS[:, None] * CT[-1]
+    return np.min(np.abs(CT[None, :] * N - rhs) / np.maximum(rhs, 1.0), axis=1)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_lut_matches_exact_rational_search(seed):
+    """Away from FP64 near-ties the oracle's matching decisions equal the exact-arithmetic ones,
+    and at the top of the source CDF (CS(s) = N) they always do."""
+    _, S, _, R, L = solved(seed=seed)
     T = oracle.target(R, L, 256, 2.2, int(S.sum()))
-    assert np.array_equal(oracle.lut(S, T, 256).astype(np.int64), brute.lut(S, T))
+    got = oracle.lut(S, T, 256).astype(np.int64)
+    want = brute.lut(S, T)
+    top = np.cumsum(S) == S.sum()
+    assert np.array_equal(got[top], want[top])
+    robust = fp64_decision_margins(S, T) > 1e-12
+    assert np.array_equal(got[robust], want[robust])
+
+
+def test_lut_top_level_survives_absorbed_tail():
+    """A target whose last occupied bins are far below the running sum's ulp: the brightest source
+    level still maps to the last occupied target level (exact arithmetic), not to where the FP64
+    running sum stopped changing."""
+    K = 16
+    S = np.zeros(K, np.uint64); S[3] = 5; S[7] = 5
+    T = np.zeros(K); T[2] = 6.0; T[5] = 4.0; T[9] = 1e-30; T[12] = 1e-40
+    lt = oracle.lut(S, T, K).astype(np.int64)
+    assert lt[7] == 12 and lt[15] == 12
+    assert np.array_equal(lt, brute.lut(S, T))
 
 
 def test_lut_is_monotone():
