@@ -140,6 +140,12 @@ const char* histretinex_status_string(hr_status s);
  * paper's method: a measurement hook. */
 hr_status histretinex_stage_times(hr_ctx* ctx, double* ms, int* calls, int reset);
 
+/* Solve-phase timestamps of image `image` of the last call (needs HR_FLAG_DEBUG_OUT): up to
+ * *count device times in nanoseconds (%globaltimer) taken by the first CTA of the image's solve
+ * at its phase boundaries (set-up, each iteration's three barriers, target, LUT), written to ns;
+ * *count is set to the number written.  Synchronises the device.  A measurement hook. */
+hr_status histretinex_profile_solve(hr_ctx* ctx, int image, long long* ns, int* count);
+
 /* Number of kernels this library launched on the context since creation (for
  * launch accounting by callers and benchmarks). */
 uint64_t histretinex_kernel_launches(const hr_ctx* ctx);

@@ -23,6 +23,7 @@ EXPORTS = (
     "histretinex_default_params", "histretinex_create", "histretinex_enhance", "histretinex_enhance_batch",
     "histretinex_enhance_host", "histretinex_get_debug", "histretinex_sync_status", "histretinex_destroy",
     "histretinex_status_string", "histretinex_kernel_launches", "histretinex_stage_times",
+    "histretinex_profile_solve",
 )
 
 
@@ -74,6 +75,8 @@ def _lib():
         L.histretinex_kernel_launches.restype = ctypes.c_uint64
         L.histretinex_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i), i]
         L.histretinex_stage_times.restype = ctypes.c_int
+        L.histretinex_profile_solve.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(i)]
+        L.histretinex_profile_solve.restype = ctypes.c_int
         for name in ("histretinex_create", "histretinex_enhance", "histretinex_enhance_batch",
                      "histretinex_enhance_host", "histretinex_get_debug", "histretinex_sync_status",
                      "histretinex_destroy"):
@@ -245,6 +248,13 @@ class Context:
         calls = ctypes.c_int(0)
         _check(_lib().histretinex_stage_times(self._h, ms, ctypes.byref(calls), int(reset)), "histretinex_stage_times")
         return ms[0], ms[1], ms[2], calls.value
+
+    def profile_solve(self, image: int = 0):
+        """Solve-phase timestamps (ns) of the last call (needs Params(debug=True))."""
+        buf = (ctypes.c_longlong * 32)()
+        n = ctypes.c_int(32)
+        _check(_lib().histretinex_profile_solve(self._h, image, buf, ctypes.byref(n)), "histretinex_profile_solve")
+        return list(buf[: n.value])
 
     def kernel_launches(self) -> int:
         return int(_lib().histretinex_kernel_launches(self._h))

@@ -56,7 +56,7 @@ SlotLayout make_layout(int K) {
   L.T = o; o += (size_t)K * 8;
   L.lut = o; o += (size_t)K * 2;
   o = align256(o);
-  L.misc = o; o += 16;
+  L.misc = o; o += 16 + (size_t)hr::kProfSlots * 8;
   o = align256(o);
   L.vec = o; o += (K > 1024) ? (size_t)kSolveVecs * K * 8 : 0;
   o = align256(o);
@@ -251,6 +251,7 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
   a.lay = c->lay;
   a.status = c->d_status;
   a.vec_in_smem = K <= 1024 ? 1 : 0;
+  a.profile = (c->p.flags & HR_FLAG_DEBUG_OUT) ? 1 : 0;
   HR_CUDA(hr::launch_solve(a, n, st));
   if (ev) HR_CUDA(cudaEventRecord(ev[2], st));
   HR_CUDA(hr::launch_apply(c->d_imgs, n, c->d_tile_start, (int)total, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay,
@@ -380,6 +381,22 @@ hr_status histretinex_get_debug(hr_ctx* c, int image, uint64_t* S, uint64_t* G, 
     HR_CUDA(cudaMemcpy(m, slot + c->lay.misc, sizeof(m), cudaMemcpyDeviceToHost));
     *iters = m[0];
   }
+  return HR_OK;
+}
+
+hr_status histretinex_profile_solve(hr_ctx* c, int image, long long* ns, int* count) {
+  if (!c || !ns || !count || image < 0 || image >= c->last_n) return HR_ERR_INVALID_ARG;
+  if (!(c->p.flags & HR_FLAG_DEBUG_OUT)) return HR_ERR_INVALID_ARG;
+  HR_CUDA(cudaSetDevice(c->device));
+  HR_CUDA(cudaDeviceSynchronize());
+  long long buf[hr::kProfSlots];
+  HR_CUDA(cudaMemcpy(buf, c->d_slots + (size_t)image * c->lay.bytes + c->lay.misc + 16, sizeof(buf),
+                     cudaMemcpyDeviceToHost));
+  int n = 0;
+  while (n < hr::kProfSlots && buf[n] != 0) ++n;
+  const int m = n < *count ? n : *count;
+  for (int i = 0; i < m; ++i) ns[i] = buf[i];
+  *count = m;
   return HR_OK;
 }
 

@@ -13,6 +13,14 @@ enum : unsigned { kStRange = 1u, kStTimeout = 2u, kStUnsupported = 4u };
 // per-target combine).  Short pieces keep the FP64 dependency chains short.
 constexpr int kPiece = 8;
 
+// Phase timestamps (ns) the solve kernel records when asked (a measurement hook).
+constexpr int kProfSlots = 32;
+
+// Shared-memory capacities of the solver's own cell list, pieces and piece sums; a CTA whose
+// share is larger keeps them in its global workspace instead.
+constexpr int kListCap = 20480;
+constexpr int kPieceCap = 3072;
+
 // One image of a launch: device pointers and geometry.
 struct ImageDesc {
   const uint8_t* in;
@@ -27,7 +35,7 @@ struct SlotLayout {
   size_t S, G;          // uint32[K] each: H_C(S), H_C(grad S)
   size_t R, L, T;       // double[K] each: results of Algorithm 1 and Eq. 20 (level-indexed)
   size_t lut;           // uint16[K]
-  size_t misc;          // int[4]: iterations, nR, nL, cells
+  size_t misc;          // int[4]: iterations, nR, nL, cells; then long long[kProfSlots] phase times
   size_t vec;           // solver vectors when they do not fit in shared memory
   size_t cls;           // uint32[4*K]: class size, cell start, first piece, piece count
   size_t list;          // uint32[K*K]: class-major cell list, (a << 16) | b
@@ -54,6 +62,7 @@ struct SolveArgs {
   SlotLayout lay;
   unsigned* status;
   int vec_in_smem;           // 1: solver vectors in dynamic shared memory
+  int profile;               // 1: record phase timestamps into the slot's misc area
 };
 
 // Launchers (return cudaError_t of the launch).

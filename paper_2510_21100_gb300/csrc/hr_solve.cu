@@ -1,33 +1,52 @@
 // Histogram-domain solve of HistRetinex on sm_103a: Algorithm 1 (Eq. 11-15), the enhanced
 // histogram (Eq. 17-20) and the histogram-matching LUT (Sec. III.C, last paragraph).
 //
-// One CTA per image.  The K x K histogram count/location matrices of Eq. 6-7 are never
-// materialised: they are rank one (R_i L_j / N) and the class of cell (i, j) is
-// index(i, j) = round(i j / (K-1)) (i = reflectance bin, j = illumination bin).  With the
-// weights of Eq. 11, K_ij = R_i L_j / P_k (P_k = class total), the sums of Eq. 13 and Eq. 12
-// factor into
+// The K x K histogram count/location matrices of Eq. 6-7 are never materialised: they are
+// rank one (R_i L_j / N) and the class of cell (i, j) is index(i, j) = round(i j / (K-1))
+// (i = reflectance bin, j = illumination bin).  With the weights of Eq. 11,
+// K_ij = R_i L_j / P_k (P_k = class total), the sums of Eq. 13 and Eq. 12 factor into
 //     R'_i = ((R_i / N) sum_j L_j^2 q_idx(i,j) + beta G_i) / (sum_j L_j^2 / N^2 + beta)
 //     L'_j = ((L_j / N) sum_i R'_i R_i q_idx(i,j) + alpha S_j) / (sum_i R'_i^2 / N^2 + alpha)
-// with q_k = S_k / P_k.  Only cells whose reflectance and illumination bins are both occupied
-// contribute (zero terms), so every sum runs over the compacted supports supp G x supp S.
+// with q_k = S_k / P_k.  Cells whose reflectance or illumination bin is empty contribute zero,
+// so every sum runs over the compacted supports supp G x supp S.
 //
 // Arithmetic is FP64.  GB300 issues one 32-lane FP64 instruction per 64 cycles per SM
-// sub-partition, so the work is cut into fixed-length pieces (kPiece cells, one lane each):
-// every FP64 instruction carries 32 useful lanes and no dependency chain is longer than
-// kPiece plus a short combine.  The summation order differs from a left-to-right loop; sums
-// of non-negative terms then agree to a few ulps per term.
+// sub-partition (an FP64 dependency chain costs 64 cycles a step), so the kernel keeps chains
+// short and lanes full: class totals over fixed-length pieces of a class-major cell list,
+// row and column sums over lane groups with shuffle trees, divisions as a hardware reciprocal
+// estimate refined by two Newton steps.  One image runs on a cluster of C CTAs (C = 16 for a
+// single image, C = 1 for batches): each CTA owns a slice of the classes, rows and columns,
+// pushes its results into every CTA's shared memory (distributed shared memory) and meets the
+// others at three cluster barriers per iteration.  The summation order differs from a
+// left-to-right loop; sums of non-negative terms then agree to a few ulps per term.
+#include <cooperative_groups.h>
+
 #include "hr_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace hr {
 namespace {
 
 constexpr int NT = kSolveThreads;
 constexpr int NW = NT / 32;
+constexpr int kMaxCluster = 16;
+constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ int iceil_div(int a, int b) { return (a + b - 1) / b; }
 
+// x / d as x * (1/d): reciprocal estimate refined by two Newton steps (error about one ulp).
+__device__ __forceinline__ double rcp64(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+
 // index(i, j) = floor((2 i j + K - 1) / (2 (K - 1))): nearest level to i j / (K - 1).
-// n < 2^25 for K <= 4096, so a float quotient is within one of the true one.
+// The quotient is < K <= 4096, so a float estimate is within one of it.
 __device__ __forceinline__ int class_index(int i, int j, int km1, float inv_d) {
   const int n = 2 * i * j + km1, d = 2 * km1;
   int q = __float2int_rz(__int2float_rn(n) * inv_d);
@@ -36,13 +55,18 @@ __device__ __forceinline__ int class_index(int i, int j, int km1, float inv_d) {
   return q;
 }
 
-// First illumination bin j with index(i, j) >= k.
+// First illumination bin j with index(i, j) >= k: ceil((2k-1)(K-1) / (2i)), at most K.
 __device__ __forceinline__ int jstart_index(int i, int k, int K) {
   if (k <= 0) return 0;
   if (i == 0) return K;
-  const long long t = (long long)(2 * k - 1) * (K - 1);
-  const long long v = (t + 2LL * i - 1) / (2LL * i);
-  return v > K ? K : (int)v;
+  const int t = (2 * k - 1) * (K - 1), d = 2 * i;
+  if (t > d * K) return K;
+  int q = __float2int_rz(__int2float_rn(t) / __int2float_rn(d));  // |error| < 1 here (q <= K)
+  int r = t - q * d;
+  while (r < 0) { --q; r += d; }
+  while (r >= d) { ++q; r -= d; }
+  q += (r > 0);
+  return q < K ? q : K;
 }
 
 struct JsIndex {
@@ -55,28 +79,12 @@ struct JsTable {  // per-context table for index_1 (Eq. 19)
   __device__ int operator()(int i, int k) const { return k >= K ? K : (int)tab[(size_t)i * (K + 1) + k]; }
 };
 
-// Deterministic block sum (fixed shuffle tree per warp, then over warps).
-__device__ double block_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    double r = l < NW ? red[l] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-    if (l == 0) red[NW] = r;
-  }
-  __syncthreads();
-  return red[NW];
-}
-
 // Exclusive block scan of one unsigned per thread; *total gets the sum.
 __device__ unsigned block_exscan(unsigned v, unsigned* red, unsigned* total) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   unsigned x = v;
   for (int o = 1; o < 32; o <<= 1) {
-    unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+    unsigned y = __shfl_up_sync(FULL, x, o);
     if (l >= o) x += y;
   }
   __syncthreads();
@@ -85,7 +93,7 @@ __device__ unsigned block_exscan(unsigned v, unsigned* red, unsigned* total) {
   if (w == 0) {
     unsigned s = l < NW ? red[l] : 0u;
     for (int o = 1; o < 32; o <<= 1) {
-      unsigned y = __shfl_up_sync(0xffffffffu, s, o);
+      unsigned y = __shfl_up_sync(FULL, s, o);
       if (l >= o) s += y;
     }
     if (l < NW) red[l] = s;
@@ -97,7 +105,7 @@ __device__ unsigned block_exscan(unsigned v, unsigned* red, unsigned* total) {
   return before;
 }
 
-// Exclusive scan of arr[0..n) in place (n <= K), returns the total.
+// Exclusive scan of arr[0..n) in place, returns the total.
 __device__ unsigned block_exscan_array(unsigned* arr, int n, unsigned* red) {
   const int per = iceil_div(n, NT);
   const int b0 = threadIdx.x * per, b1 = min(n, b0 + per);
@@ -110,76 +118,201 @@ __device__ unsigned block_exscan_array(unsigned* arr, int n, unsigned* red) {
   return total;
 }
 
-// Builds the class-major cell list for the classes cls_level(c), c in [0, ncls): for each class
-// the cells (a, b) with jstart(i, k) <= LJ[b] < jstart(i, k+1), rows a ascending, then b ascending,
-// and cuts each class into pieces of at most kPiece cells.  Returns the number of pieces.
-template <class JS, class CL>
-__device__ int build_class_lists(int nR, int ncls, const uint16_t* RI, const uint16_t* posL, JS js, CL cls_level,
-                                 unsigned* csize, unsigned* cstart, unsigned* pfirst, unsigned* pcount,
-                                 unsigned* list, uint2* piece, unsigned* ured) {
-  for (int c = threadIdx.x; c < ncls; c += NT) {
-    const int k = cls_level(c);
-    unsigned sz = 0;
-    for (int a = 0; a < nR; ++a) {
-      const int i = RI[a];
-      sz += (unsigned)(posL[js(i, k + 1)] - posL[js(i, k)]);
-    }
-    csize[c] = sz;
-    cstart[c] = sz;
-    pcount[c] = (sz + kPiece - 1) / kPiece;
-    pfirst[c] = pcount[c];
-  }
-  __syncthreads();
-  block_exscan_array(cstart, ncls, ured);
-  const unsigned npieces = block_exscan_array(pfirst, ncls, ured);
-  for (int c = threadIdx.x; c < ncls; c += NT) {
-    const int k = cls_level(c);
-    unsigned pos = cstart[c];
-    for (int a = 0; a < nR; ++a) {
-      const int i = RI[a];
-      const int lo = posL[js(i, k)], hi = posL[js(i, k + 1)];
-      for (int b = lo; b < hi; ++b) list[pos++] = ((unsigned)a << 16) | (unsigned)b;
-    }
-    const unsigned sz = csize[c], p0 = pfirst[c], np = pcount[c];
-    for (unsigned p = 0; p < np; ++p) {
-      const unsigned len = min((unsigned)kPiece, sz - p * kPiece);
-      piece[p0 + p] = make_uint2(cstart[c] + p * kPiece, len | ((unsigned)c << 16));
-    }
-  }
-  __syncthreads();
-  return (int)npieces;
+// Number of i in [0, n) with f(i) true, over the block.
+template <class F>
+__device__ unsigned block_count(int n, F f, unsigned* red) {
+  unsigned c = 0;
+  for (int i = threadIdx.x; i < n; i += NT) c += f(i) ? 1u : 0u;
+  unsigned total;
+  block_exscan(c, red, &total);
+  return total;
 }
 
-// Sums the pieces p0 .. p0+np-1 of every class c in [0, ncls) and hands the total to emit(c, total).
-// Classes with few pieces are summed by one lane each; larger ones by a whole warp (strided lane
-// sums, then a fixed shuffle tree), so no FP64 chain is longer than about np/32 + 5.
+// Sum over the lanes of one warp (lane-strided, then a fixed shuffle tree); used from lane 0.
+template <class F>
+__device__ __forceinline__ double warp_sum(int n, F f) {
+  const int l = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = l; i < n; i += 32) s += f(i);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+  return s;
+}
+
+// Copies arr[lo..hi) of this CTA into the same entries of every other CTA of the cluster; the
+// (C-1) x n remote stores are spread over the whole block, one or two per thread.
+template <typename T>
+__device__ __forceinline__ void push_slice(const cg::cluster_group& cl, T* arr, int lo, int hi, int C, int rank) {
+  const int n = hi - lo;
+  if (C == 1 || n <= 0) return;
+  for (int t = threadIdx.x; t < n * (C - 1); t += NT) {
+    const int r0 = t / n, idx = lo + (t - r0 * n);
+    const int r = r0 >= rank ? r0 + 1 : r0;
+    cl.map_shared_rank(arr, r)[idx] = arr[idx];
+  }
+}
+
+// Same for the entries arr[map[c]], c in [lo, hi).
+template <typename T>
+__device__ __forceinline__ void push_mapped(const cg::cluster_group& cl, T* arr, const uint16_t* map, int lo, int hi,
+                                            int C, int rank) {
+  const int n = hi - lo;
+  if (C == 1 || n <= 0) return;
+  for (int t = threadIdx.x; t < n * (C - 1); t += NT) {
+    const int r0 = t / n, idx = map[lo + (t - r0 * n)];
+    const int r = r0 >= rank ? r0 + 1 : r0;
+    cl.map_shared_rank(arr, r)[idx] = arr[idx];
+  }
+}
+
+__device__ __forceinline__ long long global_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Class-major cell lists.  For class c (level cls_level(c)), row a contributes the support
+// columns b with jstart(i, k) <= LJ[b] < jstart(i, k+1).  Every CTA computes the sizes of all
+// ncls classes (csz), their cell starts (cst) and piece starts (pst); each CTA then writes the
+// cells and pieces of its own classes [cA, cB), a contiguous range balanced by cell count.
+struct ClassPlan {
+  int cA, cB;          // own classes
+  unsigned pA, pB;     // own pieces
+  unsigned cells;      // total cells over all classes
+  unsigned cell0;      // first own cell (global class-major index)
+  unsigned* listp;     // own cells, indexed by (cell - cell0)
+  uint2* piecep;       // own pieces, indexed by (piece - pA)
+  double* partp;       // own piece sums, indexed by (piece - pbase)
+  unsigned pbase;      // pA for shared-memory buffers, 0 for the global workspace
+};
+
+// Own cell list, pieces and piece sums: shared-memory buffers when they fit, else the global
+// workspace (same indexing either way).
+struct OwnBufs {
+  unsigned* s_list; uint2* s_piece; double* s_part;   // shared memory
+  unsigned* g_list; uint2* g_piece; double* g_part;   // global workspace
+};
+
+template <class JS, class CL>
+__device__ ClassPlan plan_classes(const cg::cluster_group& cl, int nR, int ncls, const uint16_t* RI,
+                                  const uint16_t* posL, JS js, CL cls_level, unsigned* csz, unsigned* cst,
+                                  unsigned* pst, const OwnBufs& ob, unsigned* ured, int rank, int C) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  // class sizes, split over the cluster (warp per class, lanes over rows), then gathered
+  const int sA = (int)((long long)ncls * rank / C), sB = (int)((long long)ncls * (rank + 1) / C);
+  for (int c = sA + w; c < sB; c += NW) {
+    const int k = cls_level(c);
+    unsigned s = 0;
+#pragma unroll 4
+    for (int a = l; a < nR; a += 32) {
+      const int i = RI[a];
+      s += (unsigned)(posL[js(i, k + 1)] - posL[js(i, k)]);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if (l == 0) csz[c] = s;
+  }
+  __syncthreads();
+  push_slice(cl, csz, sA, sB, C, rank);
+  cl.sync();
+  for (int c = threadIdx.x; c < ncls; c += NT) { cst[c] = csz[c]; pst[c] = (csz[c] + kPiece - 1) / kPiece; }
+  __syncthreads();
+  ClassPlan P;
+  P.cells = block_exscan_array(cst, ncls, ured);
+  const unsigned npieces = block_exscan_array(pst, ncls, ured);
+  const unsigned lo = (unsigned)(((unsigned long long)P.cells * rank) / C);
+  const unsigned hi = (unsigned)(((unsigned long long)P.cells * (rank + 1)) / C);
+  P.cA = rank == 0 ? 0 : (int)block_count(ncls, [&](int c) { return cst[c] < lo; }, ured);
+  P.cB = rank == C - 1 ? ncls : (int)block_count(ncls, [&](int c) { return cst[c] < hi; }, ured);
+  if (P.cB < P.cA) P.cB = P.cA;
+  P.pA = P.cA < ncls ? pst[P.cA] : npieces;
+  P.pB = P.cB < ncls ? pst[P.cB] : npieces;
+  P.cell0 = P.cA < ncls ? cst[P.cA] : P.cells;
+  const unsigned cell1 = P.cB < ncls ? cst[P.cB] : P.cells;
+  if (cell1 - P.cell0 <= (unsigned)kListCap && P.pB - P.pA <= (unsigned)kPieceCap) {
+    P.listp = ob.s_list; P.piecep = ob.s_piece; P.partp = ob.s_part;
+  } else {
+    P.listp = ob.g_list; P.piecep = ob.g_piece; P.partp = ob.g_part;  // whole-image indexing
+    P.cell0 = 0;
+  }
+  P.pbase = (P.listp == ob.s_list) ? P.pA : 0u;
+  const unsigned pbase = P.pbase;
+  for (int c = P.cA + w; c < P.cB; c += NW) {  // own cells: warp per class, lanes over rows
+    const int k = cls_level(c);
+    unsigned base = cst[c];
+    for (int a0 = 0; a0 < nR; a0 += 32) {
+      const int a = a0 + l;
+      int lo_b = 0, cnt = 0;
+      if (a < nR) {
+        const int i = RI[a];
+        lo_b = posL[js(i, k)];
+        cnt = posL[js(i, k + 1)] - lo_b;
+      }
+      unsigned x = (unsigned)cnt;
+      for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(FULL, x, o);
+        if (l >= o) x += y;
+      }
+      const unsigned at = base + x - (unsigned)cnt - P.cell0;
+      for (int t = 0; t < cnt; ++t) P.listp[at + t] = ((unsigned)a << 16) | (unsigned)(lo_b + t);
+      base += __shfl_sync(FULL, x, 31);
+    }
+    const unsigned np = (csz[c] + kPiece - 1) / kPiece;
+    for (unsigned p = l; p < np; p += 32) {
+      const unsigned len = min((unsigned)kPiece, csz[c] - p * kPiece);
+      P.piecep[pst[c] + p - pbase] = make_uint2(cst[c] + p * kPiece - P.cell0, len | ((unsigned)c << 16));
+    }
+  }
+  __syncthreads();
+  return P;
+}
+
+// Sums the own pieces into the piece sums, then each own class's pieces; emit(c, total).
+// Small classes are summed by one lane, larger ones by a warp (strided sums + shuffle tree).
 template <class EMIT>
-__device__ void combine_classes(const double* part, const unsigned* pfirst, const unsigned* pcount, int ncls,
-                                EMIT emit) {
+__device__ void class_totals(const ClassPlan& P, const unsigned* csz, const unsigned* pst, const double* Rc,
+                             const double* Lc, EMIT emit) {
+  const unsigned pbase = P.pbase;
+  for (unsigned p = P.pA + threadIdx.x; p < P.pB; p += NT) {
+    const uint2 pc = P.piecep[p - pbase];
+    const unsigned len = pc.y & 0xffffu;
+    const unsigned* cells = P.listp + pc.x;
+    double acc = 0.0;
+    for (unsigned c = 0; c < len; ++c) {
+      const unsigned cell = cells[c];
+      acc = fma(Rc[cell >> 16], Lc[cell & 0xffffu], acc);
+    }
+    P.partp[p - pbase] = acc;
+  }
+  __syncthreads();
   constexpr unsigned kSmall = 4;
-  for (int c = threadIdx.x; c < ncls; c += NT) {
-    const unsigned p0 = pfirst[c], np = pcount[c];
+  for (int c = P.cA + threadIdx.x; c < P.cB; c += NT) {
+    const unsigned np = (csz[c] + kPiece - 1) / kPiece;
     if (np > kSmall) continue;
+    const double* ps = P.partp + (pst[c] - pbase);
     double s = 0.0;
-    for (unsigned p = 0; p < np; ++p) s += part[p0 + p];
+    for (unsigned p = 0; p < np; ++p) s += ps[p];
     emit(c, s);
   }
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  for (int c = w; c < ncls; c += NW) {
-    const unsigned p0 = pfirst[c], np = pcount[c];
+  for (int c = P.cA + w; c < P.cB; c += NW) {
+    const unsigned np = (csz[c] + kPiece - 1) / kPiece;
     if (np <= kSmall) continue;
+    const double* ps = P.partp + (pst[c] - pbase);
     double s = 0.0;
-    for (unsigned p = l; p < np; p += 32) s += part[p0 + p];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    for (unsigned p = l; p < np; p += 32) s += ps[p];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
     if (l == 0) emit(c, s);
   }
 }
 
 __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double conv[2][NW];
+  const cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
   const int K = A.K;
-  const int tid = threadIdx.x;
-  uint8_t* slot = A.slots + (size_t)blockIdx.x * A.slot_bytes;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint8_t* slot = A.slots + (size_t)(blockIdx.x / C) * A.slot_bytes;
   const SlotLayout& lay = A.lay;
   const unsigned* S = reinterpret_cast<const unsigned*>(slot + lay.S);
   const unsigned* G = reinterpret_cast<const unsigned*>(slot + lay.G);
@@ -188,38 +321,50 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   double* Tout = reinterpret_cast<double*>(slot + lay.T);
   uint16_t* lut = reinterpret_cast<uint16_t*>(slot + lay.lut);
   int* misc = reinterpret_cast<int*>(slot + lay.misc);
-  unsigned* cls = reinterpret_cast<unsigned*>(slot + lay.cls);
-  unsigned* list = reinterpret_cast<unsigned*>(slot + lay.list);
-  uint2* piece = reinterpret_cast<uint2*>(slot + lay.piece);
-  double* part = reinterpret_cast<double*>(slot + lay.part);
+  long long* prof = reinterpret_cast<long long*>(slot + lay.misc + 16);
+  const bool stamping = A.profile && rank == 0 && tid == 0;
+  int nstamp = 0;
+  auto stamp = [&]() { if (stamping && nstamp < kProfSlots) prof[nstamp++] = global_ns(); };
+  if (stamping)
+    for (int i = 0; i < kProfSlots; ++i) prof[i] = 0;
+  stamp();
 
-  // shared memory: index arrays, reduction scratch, then (optionally) the solver vectors
-  uint16_t* RI = reinterpret_cast<uint16_t*>(smem);
-  uint16_t* LJ = RI + K;
-  uint16_t* posL = LJ + K;  // posL[j] = number of occupied S levels below j, j in [0, K]
+  // ---- shared memory ------------------------------------------------------------------------
+  uint16_t* RI = reinterpret_cast<uint16_t*>(smem);   // occupied reflectance (gradient) levels
+  uint16_t* LJ = RI + K;                                // occupied illumination (value) levels
+  uint16_t* posL = LJ + K;                              // posL[j] = #occupied value levels below j
   size_t off = ((size_t)(3 * K + 1) * sizeof(uint16_t) + 15) & ~(size_t)15;
-  double* red = reinterpret_cast<double*>(smem + off);
-  off += (NW + 2) * sizeof(double);
-  unsigned* ured = reinterpret_cast<unsigned*>(smem + off);
-  off += ((NW + 2) * sizeof(unsigned) + 15) & ~(size_t)15;
+  unsigned* csz = reinterpret_cast<unsigned*>(smem + off); off += (size_t)K * 4;
+  unsigned* cst = reinterpret_cast<unsigned*>(smem + off); off += (size_t)K * 4;
+  unsigned* pst = reinterpret_cast<unsigned*>(smem + off); off += (size_t)K * 4;
+  double* scal = reinterpret_cast<double*>(smem + off); off += 8 * sizeof(double);
+  unsigned* ured = reinterpret_cast<unsigned*>(smem + off); off += ((NW + 2) * sizeof(unsigned) + 15) & ~(size_t)15;
+  double* scr = reinterpret_cast<double*>(smem + off); off += NT * sizeof(double);   // LUT scans
+  OwnBufs ob;
+  ob.s_part = reinterpret_cast<double*>(smem + off); off += (size_t)kPieceCap * sizeof(double);
+  ob.s_piece = reinterpret_cast<uint2*>(smem + off); off += (size_t)kPieceCap * sizeof(uint2);
+  ob.s_list = reinterpret_cast<unsigned*>(smem + off); off += (size_t)kListCap * sizeof(unsigned);
+  ob.g_list = reinterpret_cast<unsigned*>(slot + lay.list);
+  ob.g_piece = reinterpret_cast<uint2*>(slot + lay.piece);
+  ob.g_part = reinterpret_cast<double*>(slot + lay.part);
   double* vec = A.vec_in_smem ? reinterpret_cast<double*>(smem + off) : reinterpret_cast<double*>(slot + lay.vec);
-  double* Rc = vec;           // R on supp G (compacted)
-  double* Lc = vec + K;       // L on supp S (compacted)
-  double* L2c = vec + 2 * K;  // L^2
-  double* RRc = vec + 3 * K;  // R' R
-  double* Ru = vec + 4 * K;   // Eq. 13 result before Eq. 15
-  double* Lu = vec + 5 * K;   // Eq. 12 result before Eq. 14
-  double* q = vec + 6 * K;    // S_k / P_k, level-indexed
-  double* Sd = vec + 7 * K;   // S as double, level-indexed
+  double* Rc = vec;           // H_C(R) on supp G (compacted)
+  double* Lc = vec + K;       // H_C(L) on supp S (compacted)
+  double* L2c = vec + 2 * K;  // L^2 (compacted); column sums of Eq. 12; the enhanced histogram at the end
+  double* RRc = vec + 3 * K;  // R' R (compacted)
+  double* Ru = vec + 4 * K;   // Eq. 13 before Eq. 15
+  double* Lu = vec + 5 * K;   // Eq. 12 before Eq. 14
+  double* q = vec + 6 * K;    // S_k / P_k (level-indexed)
+  double* Sd = vec + 7 * K;   // S as double (level-indexed)
 
-  // ---- supports and N --------------------------------------------------------------------
+  // ---- supports and N (every CTA) -------------------------------------------------------------
   const int per = iceil_div(K, NT);
   const int k0 = tid * per, k1 = min(K, k0 + per);
-  unsigned cr = 0, cl = 0, nsum = 0;
-  for (int k = k0; k < k1; ++k) { cr += G[k] > 0u; cl += S[k] > 0u; nsum += S[k]; }
-  unsigned nR, nL, Nu;
-  unsigned offR = block_exscan(cr, ured, &nR);
-  unsigned offL = block_exscan(cl, ured, &nL);
+  unsigned cr = 0, cl_ = 0, nsum = 0;
+  for (int k = k0; k < k1; ++k) { cr += G[k] > 0u; cl_ += S[k] > 0u; nsum += S[k]; }
+  unsigned nRu, nLu, Nu;
+  unsigned offR = block_exscan(cr, ured, &nRu);
+  unsigned offL = block_exscan(cl_, ured, &nLu);
   block_exscan(nsum, ured, &Nu);
   for (int k = k0; k < k1; ++k) {
     if (G[k] > 0u) RI[offR++] = (uint16_t)k;
@@ -228,145 +373,164 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     Sd[k] = (double)S[k];
     q[k] = 0.0;
   }
-  if (tid == 0) posL[K] = (uint16_t)nL;
+  if (tid == 0) posL[K] = (uint16_t)nLu;
   __syncthreads();
+  const int nR = (int)nRu, nL = (int)nLu;
   const double N = (double)Nu;
-  const double NN = N * N;
+  const double invN = rcp64(N);
+  const double invNN = rcp64(N * N);
   const int km1 = K - 1;
   const float inv_d = 1.0f / (float)(2 * km1);
 
-  // ---- class-major cell list for the classes of Eq. 11 that matter (S_k > 0) --------------
-  unsigned* csize = cls;
-  unsigned* cstart = cls + K;
-  unsigned* pfirst = cls + 2 * K;
-  unsigned* pcount = cls + 3 * K;
-  const int nP = build_class_lists(nR, nL, RI, posL, JsIndex{K}, [&](int c) { return (int)LJ[c]; }, csize, cstart,
-                                   pfirst, pcount, list, piece, ured);
+  // ---- Eq. 11 classes that matter (S_k > 0): plan and own cell lists -------------------------
+  cl.sync();  // every CTA of the cluster has started before any distributed shared memory access
+  stamp();
+  const ClassPlan PP = plan_classes(cl, nR, nL, RI, posL, JsIndex{K}, [&](int c) { return (int)LJ[c]; }, csz, cst,
+                                    pst, ob, ured, rank, C);
+  stamp();
+  // own rows and columns of the updates (contiguous slices)
+  const int aA = (int)((long long)nR * rank / C), aB = (int)((long long)nR * (rank + 1) / C);
+  const int bA = (int)((long long)nL * rank / C), bB = (int)((long long)nL * (rank + 1) / C);
+  const int GA = C == 1 ? 4 : 16;   // lanes per row in the Eq. 13 sums
+  const int GB = C == 1 ? 4 : 32;   // lanes per column in the Eq. 12 sums
+  // (one image's arithmetic depends on C only through these group sizes and the class split)
 
-  for (int a = tid; a < (int)nR; a += NT) Rc[a] = (double)G[RI[a]];   // R^(0) = H_C(grad S)
-  for (int b = tid; b < (int)nL; b += NT) Lc[b] = (double)S[LJ[b]];   // L^(0) = H_C(S)
+  for (int a = tid; a < nR; a += NT) Rc[a] = (double)G[RI[a]];   // R^(0) = H_C(grad S)
+  for (int b = tid; b < nL; b += NT) Lc[b] = (double)S[LJ[b]];   // L^(0) = H_C(S)
   __syncthreads();
 
-  const int nCa = iceil_div((int)nL, kPiece), nPA = (int)nR * nCa;
-  const int nCb = iceil_div((int)nR, kPiece), nPB = (int)nL * nCb;
   int it = 0;
-  for (; it < A.max_iter;) {
-    // Eq. 11: class totals P_k over the class-major pieces, then q_k = S_k / P_k
-    for (int p = tid; p < nP; p += NT) {
-      const uint2 pc = piece[p];
-      const unsigned len = pc.y & 0xffffu;
-      double acc = 0.0;
-      for (unsigned c = 0; c < len; ++c) {
-        const unsigned cell = list[pc.x + c];
-        acc = fma(Rc[cell >> 16], Lc[cell & 0xffffu], acc);
-      }
-      part[p] = acc;
+  while (it < A.max_iter) {
+    // Eq. 11: class totals P_k of the own classes; q_k = S_k / P_k to every CTA.
+    if (warp == NW - 1) {  // meanwhile: 1 / denominator of Eq. 13 (from L, the same in every CTA)
+      const double sl2 = warp_sum(nL, [&](int b) { const double x = Lc[b]; return x * x; });
+      if (lane == 0) scal[0] = rcp64(fma(sl2, invNN, A.beta));
     }
-    __syncthreads();
-    combine_classes(part, pfirst, pcount, (int)nL, [&](int c, double P) {
+    for (int b = tid; b < nL; b += NT) { const double x = Lc[b]; L2c[b] = x * x; }
+    class_totals(PP, csz, pst, Rc, Lc, [&](int c, double P) {
       const int k = LJ[c];
-      q[k] = P > 0.0 ? Sd[k] / P : 0.0;
+      q[k] = P > 0.0 ? Sd[k] * rcp64(P) : 0.0;
     });
-    double sl2 = 0.0;
-    for (int b = tid; b < (int)nL; b += NT) { const double l = Lc[b]; L2c[b] = l * l; sl2 = fma(l, l, sl2); }
-    const double dR = block_sum(sl2, red) / NN + A.beta;   // (includes a __syncthreads)
+    __syncthreads();
+    push_mapped(cl, q, LJ, PP.cA, PP.cB, C, rank);
+    cl.sync();
+    if (it == 0) stamp();
 
-    // Eq. 13: reflectance update, pieces over (row a, chunk of illumination bins)
-    for (int p = tid; p < nPA; p += NT) {
-      const int a = p / nCa, ch = p - a * nCa;
-      const int i = RI[a];
-      const int b0 = ch * kPiece, b1 = min((int)nL, b0 + kPiece);
-      double acc = 0.0;
-      for (int b = b0; b < b1; ++b) acc = fma(L2c[b], q[class_index(i, LJ[b], km1, inv_d)], acc);
-      part[p] = acc;
+    // Eq. 13 for the own rows: lane groups of GA over the illumination bins.
+    {
+      const double rdR = scal[0];
+      const int gi = lane / GA, gl = lane % GA, rpw = 32 / GA;
+      for (int a0 = aA + warp * rpw; a0 < aB; a0 += NW * rpw) {
+        const int a = a0 + gi;
+        double acc = 0.0;
+        if (a < aB) {
+          const int i = RI[a];
+          for (int b = gl; b < nL; b += GA) acc = fma(L2c[b], q[class_index(i, LJ[b], km1, inv_d)], acc);
+        }
+        for (int o = GA >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        if (gl == 0 && a < aB) {
+          const double r = Rc[a];
+          const double ru = fma(r * invN, acc, A.beta * (double)G[RI[a]]) * rdR;
+          Ru[a] = ru;
+          RRc[a] = ru * r;
+        }
+      }
     }
     __syncthreads();
-    double sr2 = 0.0, sr = 0.0;
-    for (int a = tid; a < (int)nR; a += NT) {
-      double s = 0.0;
-      for (int ch = 0; ch < nCa; ++ch) s += part[a * nCa + ch];
-      const double r = Rc[a];
-      const double ru = fma(r / N, s, A.beta * (double)G[RI[a]]) / dR;
-      Ru[a] = ru;
-      RRc[a] = ru * r;
-      sr2 = fma(ru, ru, sr2);
-      sr += ru;
-    }
-    const double dL = block_sum(sr2, red) / NN + A.alpha;
-    const double sR = block_sum(sr, red);
+    push_slice(cl, Ru, aA, aB, C, rank);
+    push_slice(cl, RRc, aA, aB, C, rank);
+    cl.sync();
+    if (it == 0) stamp();
 
-    // Eq. 12: illumination update with the new R, pieces over (column b, chunk of reflectance bins)
-    for (int p = tid; p < nPB; p += NT) {
-      const int b = p / nCb, ch = p - b * nCb;
-      const int j = LJ[b];
-      const int a0 = ch * kPiece, a1 = min((int)nR, a0 + kPiece);
-      double acc = 0.0;
-      for (int a = a0; a < a1; ++a) acc = fma(RRc[a], q[class_index(RI[a], j, km1, inv_d)], acc);
-      part[p] = acc;
+    // Eq. 12 for the own columns: lane groups of GB over the reflectance bins.
+    if (warp == NW - 1) {  // meanwhile: 1 / denominator of Eq. 12 (all R', the same order in every CTA)
+      const double s2 = warp_sum(nR, [&](int a) { const double x = Ru[a]; return x * x; });
+      if (lane == 0) scal[1] = rcp64(fma(s2, invNN, A.alpha));
+    } else if (warp == NW - 2) {  // and the Eq. 15 scale N / sum R'
+      const double s1 = warp_sum(nR, [&](int a) { return Ru[a]; });
+      if (lane == 0) scal[2] = N * rcp64(s1);
+    }
+    {
+      double* Bs = L2c;  // column sums (L^2 is not needed again in this iteration)
+      const int gi = lane / GB, gl = lane % GB, cpw = 32 / GB;
+      for (int b0 = bA + warp * cpw; b0 < bB; b0 += NW * cpw) {
+        const int b = b0 + gi;
+        double acc = 0.0;
+        if (b < bB) {
+          const int j = LJ[b];
+          for (int a = gl; a < nR; a += GB) acc = fma(RRc[a], q[class_index(RI[a], j, km1, inv_d)], acc);
+        }
+        for (int o = GB >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        if (gl == 0 && b < bB) Bs[b] = acc;
+      }
+      __syncthreads();
+      const double rdL = scal[1];
+      for (int b = bA + tid; b < bB; b += NT) Lu[b] = fma(Lc[b] * invN, Bs[b], A.alpha * Sd[LJ[b]]) * rdL;
     }
     __syncthreads();
-    double sl = 0.0;
-    for (int b = tid; b < (int)nL; b += NT) {
-      double s = 0.0;
-      for (int ch = 0; ch < nCb; ++ch) s += part[b * nCb + ch];
-      const double l = Lc[b];
-      const double lu = fma(l / N, s, A.alpha * Sd[LJ[b]]) / dL;
-      Lu[b] = lu;
-      sl += lu;
-    }
-    const double sL = block_sum(sl, red);
+    push_slice(cl, Lu, bA, bB, C, rank);
+    cl.sync();
+    if (it == 0) stamp();
 
-    // Eq. 15 and Eq. 14: renormalise to mass N; squared changes for the stopping rule
+    // Eq. 15 and Eq. 14: renormalise to mass N (every CTA alike); squared changes for the stop rule.
+    if (warp == 0) {  // Eq. 14 scale N / sum L' (all L', the same order in every CTA)
+      const double s1 = warp_sum(nL, [&](int b) { return Lu[b]; });
+      if (lane == 0) scal[3] = N * rcp64(s1);
+    }
+    __syncthreads();
+    const double sc_r = scal[2], sc_l = scal[3];
     double dr = 0.0, dl = 0.0;
-    for (int a = tid; a < (int)nR; a += NT) {
-      const double rn = (N * Ru[a]) / sR;
+    for (int a = tid; a < nR; a += NT) {
+      const double rn = Ru[a] * sc_r;
       const double d = rn - Rc[a];
       dr = fma(d, d, dr);
       Rc[a] = rn;
     }
-    for (int b = tid; b < (int)nL; b += NT) {
-      const double ln = (N * Lu[b]) / sL;
+    for (int b = tid; b < nL; b += NT) {
+      const double ln = Lu[b] * sc_l;
       const double d = ln - Lc[b];
       dl = fma(d, d, dl);
       Lc[b] = ln;
     }
     ++it;
+    stamp();
     if (!A.fixed_iters) {
-      const double DR = block_sum(dr, red);
-      const double DL = block_sum(dl, red);
+      // identical data and order in every CTA, so every CTA takes the same decision
+      for (int o = 16; o > 0; o >>= 1) {
+        dr += __shfl_xor_sync(FULL, dr, o);
+        dl += __shfl_xor_sync(FULL, dl, o);
+      }
+      if (lane == 0) { conv[0][warp] = dr; conv[1][warp] = dl; }
+      __syncthreads();
+      double DR = 0.0, DL = 0.0;
+      for (int w2 = 0; w2 < NW; ++w2) { DR += conv[0][w2]; DL += conv[1][w2]; }
+      __syncthreads();
       if (DR <= A.eps && DL <= A.eps) break;
     } else {
       __syncthreads();
     }
   }
 
-  // ---- Eq. 17-20: enhanced histogram through the index_1 class map ------------------------
-  const int nPT = build_class_lists(nR, K, RI, posL, JsTable{A.jstart1, K}, [](int c) { return c; }, csize, cstart,
-                                    pfirst, pcount, list, piece, ured);
-  for (int p = tid; p < nPT; p += NT) {
-    const uint2 pc = piece[p];
-    const unsigned len = pc.y & 0xffffu;
-    double acc = 0.0;
-    for (unsigned c = 0; c < len; ++c) {
-      const unsigned cell = list[pc.x + c];
-      acc = fma(Rc[cell >> 16], Lc[cell & 0xffffu], acc);
-    }
-    part[p] = acc;
-  }
+  // ---- Eq. 17-20: enhanced histogram through the index_1 class map -----------------------------
+  double* T = L2c;  // level-indexed target, filled by every CTA's own classes
+  for (int k = tid; k < K; k += NT) T[k] = 0.0;
+  const ClassPlan PT = plan_classes(cl, nR, K, RI, posL, JsTable{A.jstart1, K}, [](int c) { return c; }, csz, cst,
+                                    pst, ob, ured, rank, C);  // (its cluster barrier orders the zeroing)
+  stamp();
+  class_totals(PT, csz, pst, Rc, Lc, [&](int c, double s) { T[c] = s * invN; });  // count matrix carries 1/N (Eq. 6)
   __syncthreads();
-  double* T = L2c;  // reuse: level-indexed target (K entries)
-  combine_classes(part, pfirst, pcount, K, [&](int c, double s) { T[c] = s / N; });  // count matrix carries 1/N (Eq. 6)
-  __syncthreads();
+  push_slice(cl, T, PT.cA, PT.cB, C, rank);
+  cl.sync();
+  stamp();
+  if (rank != 0) return;
 
-  // ---- histogram matching LUT ---------------------------------------------------------------
-  // CT = inclusive prefix sum of T (Hillis-Steele in place over K entries, per-thread chunks)
+  // ---- histogram matching LUT (rank 0) -----------------------------------------------------------
   {
-    double* CT = RRc;  // reuse, K entries
+    double* CT = RRc;  // inclusive prefix sums of T: per-thread chunks, then the chunk offsets
     const int b0 = k0, b1 = k1;
     double s = 0.0;
     for (int k = b0; k < b1; ++k) { s += T[k]; CT[k] = s; }
-    // scan of the per-thread chunk totals (NT values) in shared memory via red-like buffer in part
-    double* tot = part;
+    double* tot = scr;
     tot[tid] = s;
     __syncthreads();
     for (int o = 1; o < NT; o <<= 1) {
@@ -379,17 +543,15 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     for (int k = b0; k < b1; ++k) CT[k] += before;
     __syncthreads();
     const double TT = CT[K - 1];
-    // rhs(s) = CS(s) * TT with CS the exact integer cumulative count of S; lhs(z) = CT(z) * N.
-    // Non-negative doubles order like their bit patterns; a running max makes lhs monotone so the
-    // first z with lhs(z) >= rhs(s) is found by binary search.
-    unsigned long long* lhs = reinterpret_cast<unsigned long long*>(Ru);  // K entries
+    // lhs(z) = CT(z) N as ordered bit patterns (non-negative doubles), made monotone by a running max
+    unsigned long long* lhs = reinterpret_cast<unsigned long long*>(Ru);
     unsigned long long m = 0;
     for (int k = b0; k < b1; ++k) {
       const unsigned long long v = (unsigned long long)__double_as_longlong(CT[k] * N);
       m = v > m ? v : m;
       lhs[k] = m;
     }
-    unsigned long long* tmax = reinterpret_cast<unsigned long long*>(part);
+    unsigned long long* tmax = reinterpret_cast<unsigned long long*>(scr);
     __syncthreads();
     tmax[tid] = m;
     __syncthreads();
@@ -419,7 +581,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
       cs += S[k];
       if (cs == Nu) { lut[k] = (uint16_t)z_top; continue; }
       const unsigned long long rhs = (unsigned long long)__double_as_longlong((double)cs * TT);
-      int lo = 0, hi = K - 1;  // lhs[K-1] >= rhs unless no z qualifies; then K-1
+      int lo = 0, hi = K - 1;  // first z with lhs(z) >= rhs; K-1 if none
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (lhs[mid] >= rhs) hi = mid; else lo = mid + 1;
@@ -429,30 +591,75 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   }
   __syncthreads();
 
-  // ---- results (level-indexed) ----------------------------------------------------------------
+  // ---- results (level-indexed) -------------------------------------------------------------------
   for (int k = tid; k < K; k += NT) { Rout[k] = 0.0; Lout[k] = 0.0; Tout[k] = T[k]; }
   __syncthreads();
-  for (int a = tid; a < (int)nR; a += NT) Rout[RI[a]] = Rc[a];
-  for (int b = tid; b < (int)nL; b += NT) Lout[LJ[b]] = Lc[b];
-  if (tid == 0) { misc[0] = it; misc[1] = (int)nR; misc[2] = (int)nL; misc[3] = nP; }
+  for (int a = tid; a < nR; a += NT) Rout[RI[a]] = Rc[a];
+  for (int b = tid; b < nL; b += NT) Lout[LJ[b]] = Lc[b];
+  if (tid == 0) { misc[0] = it; misc[1] = nR; misc[2] = nL; misc[3] = (int)PP.cells; }
+  stamp();
 }
 
 }  // namespace
 
 size_t solve_smem_bytes(int K, int vec_in_smem) {
   size_t off = ((size_t)(3 * K + 1) * sizeof(uint16_t) + 15) & ~(size_t)15;
-  off += (NW + 2) * sizeof(double);
+  off += (size_t)3 * K * 4;
+  off += 8 * sizeof(double);
   off += ((NW + 2) * sizeof(unsigned) + 15) & ~(size_t)15;
+  off += NT * sizeof(double);
+  off += (size_t)kPieceCap * (sizeof(double) + sizeof(uint2)) + (size_t)kListCap * sizeof(unsigned);
   if (vec_in_smem) off += (size_t)kSolveVecs * K * sizeof(double);
   return off;
+}
+
+// Largest cluster (16, 8, 4, 2 or 1 CTAs) that can be resident for one image; 1 for batches.
+int solve_cluster_size(int K, int n, size_t smem) {
+  if (n != 1 || K > 1024) return 1;
+  for (int C = kMaxCluster; C > 1; C >>= 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, solve_kernel, &cfg) == cudaSuccess && nclusters > 0) return C;
+    cudaGetLastError();
+  }
+  return 1;
 }
 
 cudaError_t launch_solve(const SolveArgs& a, int n, cudaStream_t st) {
   const size_t smem = solve_smem_bytes(a.K, a.vec_in_smem);
   cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  solve_kernel<<<n, NT, smem, st>>>(a);
-  return cudaGetLastError();
+  e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  static int cached_K = -1, cached_C = 1;  // per process: the cluster size for single images of this K
+  int C = 1;
+  if (n == 1 && a.K <= 1024) {
+    if (cached_K != a.K) { cached_C = solve_cluster_size(a.K, 1, smem); cached_K = a.K; }
+    C = cached_C;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n * C));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, solve_kernel, a);
 }
 
 }  // namespace hr
