@@ -200,6 +200,15 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
     total += hr::tiles_of(d.W, d.H);
   }
   if (total >= (1LL << 31)) return HR_ERR_UNSUPPORTED;
+  // 8-bit fast paths need every row 16-byte aligned (input for the histogram pass, both for apply)
+  bool fast_in = elem_bytes == 1 && K <= 256, fast_out = fast_in;
+  for (int i = 0; i < n; ++i) {
+    const ImageDesc& d = imgs[i];
+    const bool ain = ((uintptr_t)d.in % 16 == 0) && (d.in_pitch % 16 == 0);
+    const bool aout = ((uintptr_t)d.out % 16 == 0) && (d.out_pitch % 16 == 0);
+    fast_in = fast_in && ain;
+    fast_out = fast_out && ain && aout;
+  }
   hr_status s = ensure_slots(c, n);
   if (s != HR_OK) return s;
   s = ensure_desc(c, n);
@@ -236,7 +245,7 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
     HR_CUDA(cudaEventRecord(ev[0], st));
   }
   HR_CUDA(hr::launch_hist(c->d_imgs, n, c->d_tile_start, (int)total, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay,
-                          c->d_status, px_grid, st));
+                          c->d_status, px_grid, st, fast_in));
   if (ev) HR_CUDA(cudaEventRecord(ev[1], st));
   hr::SolveArgs a{};
   a.K = K;
@@ -255,7 +264,7 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
   HR_CUDA(hr::launch_solve(a, n, st));
   if (ev) HR_CUDA(cudaEventRecord(ev[2], st));
   HR_CUDA(hr::launch_apply(c->d_imgs, n, c->d_tile_start, (int)total, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay,
-                           c->d_status, px_grid, st));
+                           c->d_status, px_grid, st, fast_out));
   if (ev) HR_CUDA(cudaEventRecord(ev[3], st));
   c->launches += 3;
   c->last_n = n;

@@ -236,6 +236,7 @@ __device__ ClassPlan plan_classes(const cg::cluster_group& cl, int nR, int ncls,
   P.pbase = (P.listp == ob.s_list) ? P.pA : 0u;
   const unsigned pbase = P.pbase;
   for (int c = P.cA + w; c < P.cB; c += NW) {  // own cells: warp per class, lanes over rows
+    if (csz[c] == 0) continue;
     const int k = cls_level(c);
     unsigned base = cst[c];
     for (int a0 = 0; a0 < nR; a0 += 32) {
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   unsigned* csz = reinterpret_cast<unsigned*>(smem + off); off += (size_t)K * 4;
   unsigned* cst = reinterpret_cast<unsigned*>(smem + off); off += (size_t)K * 4;
   unsigned* pst = reinterpret_cast<unsigned*>(smem + off); off += (size_t)K * 4;
-  double* scal = reinterpret_cast<double*>(smem + off); off += 8 * sizeof(double);
+  double* scal = reinterpret_cast<double*>(smem + off); off += 8 * sizeof(double);  // per-iteration scalars
   unsigned* ured = reinterpret_cast<unsigned*>(smem + off); off += ((NW + 2) * sizeof(unsigned) + 15) & ~(size_t)15;
   double* scr = reinterpret_cast<double*>(smem + off); off += NT * sizeof(double);   // LUT scans
   OwnBufs ob;
@@ -399,26 +400,44 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   for (int b = tid; b < nL; b += NT) Lc[b] = (double)S[LJ[b]];   // L^(0) = H_C(S)
   __syncthreads();
 
+  // R = scR * R0 and L = scL * L0: the renormalisation of Eq. 15 / Eq. 14 is carried as two scales
+  // into the next iteration (computed while its class totals run) instead of a separate pass.
+  double* R0 = Rc;
+  double* L0 = Lc;
+  double* R1 = Ru;
+  double* L1 = Lu;
+  double scR = 1.0, scL = 1.0;  // R^(0) = H_C(grad S) and L^(0) = H_C(S) already have mass N
   int it = 0;
   while (it < A.max_iter) {
     // Eq. 11: class totals P_k of the own classes; q_k = S_k / P_k to every CTA.
-    if (warp == NW - 1) {  // meanwhile: 1 / denominator of Eq. 13 (from L, the same in every CTA)
-      const double sl2 = warp_sum(nL, [&](int b) { const double x = Lc[b]; return x * x; });
-      if (lane == 0) scal[0] = rcp64(fma(sl2, invNN, A.beta));
+    if (warp == NW - 1) {  // meanwhile: the L scale and 1 / denominator of Eq. 13 (every CTA alike)
+      double s1 = 0.0, s2 = 0.0;
+      for (int b = lane; b < nL; b += 32) { const double x = L0[b]; s1 += x; s2 = fma(x, x, s2); }
+      for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(FULL, s1, o);
+        s2 += __shfl_xor_sync(FULL, s2, o);
+      }
+      if (lane == 0) {
+        const double sl = it == 0 ? 1.0 : N * rcp64(s1);
+        scal[3] = sl;
+        scal[0] = rcp64(fma(s2 * (sl * sl), invNN, A.beta));
+      }
     }
-    for (int b = tid; b < nL; b += NT) { const double x = Lc[b]; L2c[b] = x * x; }
-    class_totals(PP, csz, pst, Rc, Lc, [&](int c, double P) {
+    for (int b = tid; b < nL; b += NT) { const double x = L0[b]; L2c[b] = x * x; }
+    class_totals(PP, csz, pst, R0, L0, [&](int c, double Pu) {  // (after a barrier: scal[3] is set)
       const int k = LJ[c];
+      const double P = Pu * (scR * scal[3]);
       q[k] = P > 0.0 ? Sd[k] * rcp64(P) : 0.0;
     });
     __syncthreads();
     push_mapped(cl, q, LJ, PP.cA, PP.cB, C, rank);
     cl.sync();
+    scL = scal[3];
     if (it == 0) stamp();
 
     // Eq. 13 for the own rows: lane groups of GA over the illumination bins.
     {
-      const double rdR = scal[0];
+      const double rdR = scal[0], sl2 = scL * scL;
       const int gi = lane / GA, gl = lane % GA, rpw = 32 / GA;
       for (int a0 = aA + warp * rpw; a0 < aB; a0 += NW * rpw) {
         const int a = a0 + gi;
@@ -429,26 +448,28 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         }
         for (int o = GA >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
         if (gl == 0 && a < aB) {
-          const double r = Rc[a];
-          const double ru = fma(r * invN, acc, A.beta * (double)G[RI[a]]) * rdR;
-          Ru[a] = ru;
+          const double r = scR * R0[a];
+          const double ru = fma(r * invN, acc * sl2, A.beta * (double)G[RI[a]]) * rdR;
+          R1[a] = ru;
           RRc[a] = ru * r;
         }
       }
     }
     __syncthreads();
-    push_slice(cl, Ru, aA, aB, C, rank);
+    push_slice(cl, R1, aA, aB, C, rank);
     push_slice(cl, RRc, aA, aB, C, rank);
     cl.sync();
     if (it == 0) stamp();
 
     // Eq. 12 for the own columns: lane groups of GB over the reflectance bins.
-    if (warp == NW - 1) {  // meanwhile: 1 / denominator of Eq. 12 (all R', the same order in every CTA)
-      const double s2 = warp_sum(nR, [&](int a) { const double x = Ru[a]; return x * x; });
-      if (lane == 0) scal[1] = rcp64(fma(s2, invNN, A.alpha));
-    } else if (warp == NW - 2) {  // and the Eq. 15 scale N / sum R'
-      const double s1 = warp_sum(nR, [&](int a) { return Ru[a]; });
-      if (lane == 0) scal[2] = N * rcp64(s1);
+    if (warp == NW - 1) {  // meanwhile: 1 / denominator of Eq. 12 and the next R scale N / sum R'
+      double s1 = 0.0, s2 = 0.0;
+      for (int a = lane; a < nR; a += 32) { const double x = R1[a]; s1 += x; s2 = fma(x, x, s2); }
+      for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(FULL, s1, o);
+        s2 += __shfl_xor_sync(FULL, s2, o);
+      }
+      if (lane == 0) { scal[1] = rcp64(fma(s2, invNN, A.alpha)); scal[2] = N * rcp64(s1); }
     }
     {
       double* Bs = L2c;  // column sums (L^2 is not needed again in this iteration)
@@ -465,37 +486,27 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
       }
       __syncthreads();
       const double rdL = scal[1];
-      for (int b = bA + tid; b < bB; b += NT) Lu[b] = fma(Lc[b] * invN, Bs[b], A.alpha * Sd[LJ[b]]) * rdL;
+      for (int b = bA + tid; b < bB; b += NT) L1[b] = fma(scL * L0[b] * invN, Bs[b], A.alpha * Sd[LJ[b]]) * rdL;
     }
     __syncthreads();
-    push_slice(cl, Lu, bA, bB, C, rank);
+    push_slice(cl, L1, bA, bB, C, rank);
     cl.sync();
     if (it == 0) stamp();
 
-    // Eq. 15 and Eq. 14: renormalise to mass N (every CTA alike); squared changes for the stop rule.
-    if (warp == 0) {  // Eq. 14 scale N / sum L' (all L', the same order in every CTA)
-      const double s1 = warp_sum(nL, [&](int b) { return Lu[b]; });
-      if (lane == 0) scal[3] = N * rcp64(s1);
-    }
-    __syncthreads();
-    const double sc_r = scal[2], sc_l = scal[3];
-    double dr = 0.0, dl = 0.0;
-    for (int a = tid; a < nR; a += NT) {
-      const double rn = Ru[a] * sc_r;
-      const double d = rn - Rc[a];
-      dr = fma(d, d, dr);
-      Rc[a] = rn;
-    }
-    for (int b = tid; b < nL; b += NT) {
-      const double ln = Lu[b] * sc_l;
-      const double d = ln - Lc[b];
-      dl = fma(d, d, dl);
-      Lc[b] = ln;
-    }
+    const double scR1 = scal[2];
     ++it;
-    stamp();
+    bool done = false;
     if (!A.fixed_iters) {
-      // identical data and order in every CTA, so every CTA takes the same decision
+      // squared changes of the renormalised histograms (identical data and order in every CTA)
+      if (warp == 0) {
+        const double s1 = warp_sum(nL, [&](int b) { return L1[b]; });
+        if (lane == 0) scal[4] = N * rcp64(s1);
+      }
+      __syncthreads();
+      const double scL1 = scal[4];
+      double dr = 0.0, dl = 0.0;
+      for (int a = tid; a < nR; a += NT) { const double d = scR1 * R1[a] - scR * R0[a]; dr = fma(d, d, dr); }
+      for (int b = tid; b < nL; b += NT) { const double d = scL1 * L1[b] - scL * L0[b]; dl = fma(d, d, dl); }
       for (int o = 16; o > 0; o >>= 1) {
         dr += __shfl_xor_sync(FULL, dr, o);
         dl += __shfl_xor_sync(FULL, dl, o);
@@ -504,12 +515,29 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
       __syncthreads();
       double DR = 0.0, DL = 0.0;
       for (int w2 = 0; w2 < NW; ++w2) { DR += conv[0][w2]; DL += conv[1][w2]; }
-      __syncthreads();
-      if (DR <= A.eps && DL <= A.eps) break;
-    } else {
-      __syncthreads();
+      done = DR <= A.eps && DL <= A.eps;
     }
+    double* t = R0; R0 = R1; R1 = t;
+    t = L0; L0 = L1; L1 = t;
+    scR = scR1;
+    __syncthreads();
+    stamp();
+    if (done) break;
   }
+  // renormalised results of Algorithm 1 (Eq. 15 and Eq. 14 applied to the last iterate)
+  if (warp == 0) {
+    const double s1 = warp_sum(nL, [&](int b) { return L0[b]; });
+    if (lane == 0) scal[4] = N * rcp64(s1);
+  }
+  __syncthreads();
+  {
+    const double sl = scal[4];
+    for (int a = tid; a < nR; a += NT) R1[a] = scR * R0[a];
+    for (int b = tid; b < nL; b += NT) L1[b] = sl * L0[b];
+  }
+  __syncthreads();
+  Rc = R1;
+  Lc = L1;
 
   // ---- Eq. 17-20: enhanced histogram through the index_1 class map -----------------------------
   double* T = L2c;  // level-indexed target, filled by every CTA's own classes
@@ -526,42 +554,63 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
 
   // ---- histogram matching LUT (rank 0) -----------------------------------------------------------
   {
-    double* CT = RRc;  // inclusive prefix sums of T: per-thread chunks, then the chunk offsets
+    double* CT = RRc;                                                 // inclusive prefix sums of T
+    unsigned long long* lhs = reinterpret_cast<unsigned long long*>(q);  // CT(z) N, made monotone
     const int b0 = k0, b1 = k1;
     double s = 0.0;
     for (int k = b0; k < b1; ++k) { s += T[k]; CT[k] = s; }
-    double* tot = scr;
-    tot[tid] = s;
-    __syncthreads();
-    for (int o = 1; o < NT; o <<= 1) {
-      double v = tid >= o ? tot[tid - o] : 0.0;
-      __syncthreads();
-      if (tid >= o) tot[tid] += v;
-      __syncthreads();
+    double x = s;  // inclusive scan of the per-thread chunk sums: within the warp, then over warps
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
     }
-    const double before = tid > 0 ? tot[tid - 1] : 0.0;
+    double ex = __shfl_up_sync(FULL, x, 1);
+    if (lane == 0) ex = 0.0;
+    if (lane == 31) scr[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      double wv = lane < NW ? scr[lane] : 0.0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(FULL, wv, o);
+        if (lane >= o) wv += y;
+      }
+      if (lane < NW) scr[NW + lane] = wv;
+    }
+    __syncthreads();
+    const double before = ex + (warp > 0 ? scr[NW + warp - 1] : 0.0);
     for (int k = b0; k < b1; ++k) CT[k] += before;
     __syncthreads();
     const double TT = CT[K - 1];
-    // lhs(z) = CT(z) N as ordered bit patterns (non-negative doubles), made monotone by a running max
-    unsigned long long* lhs = reinterpret_cast<unsigned long long*>(Ru);
+    // non-negative doubles order like their bit patterns; a running max makes lhs monotone so the
+    // first z with lhs(z) >= rhs(s) is found by binary search
     unsigned long long m = 0;
     for (int k = b0; k < b1; ++k) {
       const unsigned long long v = (unsigned long long)__double_as_longlong(CT[k] * N);
       m = v > m ? v : m;
       lhs[k] = m;
     }
-    unsigned long long* tmax = reinterpret_cast<unsigned long long*>(scr);
-    __syncthreads();
-    tmax[tid] = m;
-    __syncthreads();
-    for (int o = 1; o < NT; o <<= 1) {
-      unsigned long long v = tid >= o ? tmax[tid - o] : 0ull;
-      __syncthreads();
-      if (tid >= o && v > tmax[tid]) tmax[tid] = v;
-      __syncthreads();
+    unsigned long long xm = m;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(FULL, xm, o);
+      if (lane >= o && y > xm) xm = y;
     }
-    const unsigned long long pm = tid > 0 ? tmax[tid - 1] : 0ull;
+    unsigned long long exm = __shfl_up_sync(FULL, xm, 1);
+    if (lane == 0) exm = 0ull;
+    unsigned long long* wmax = reinterpret_cast<unsigned long long*>(scr);
+    __syncthreads();
+    if (lane == 31) wmax[warp] = xm;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned long long wv = lane < NW ? wmax[lane] : 0ull;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(FULL, wv, o);
+        if (lane >= o && y > wv) wv = y;
+      }
+      if (lane < NW) wmax[NW + lane] = wv;
+    }
+    __syncthreads();
+    unsigned long long pm = warp > 0 ? wmax[NW + warp - 1] : 0ull;
+    if (exm > pm) pm = exm;
     for (int k = b0; k < b1; ++k) lhs[k] = lhs[k] > pm ? lhs[k] : pm;
     // z_top: last occupied target level.  Where CS(s) = N the matching condition reads
     // CT(z) >= TT, which in exact arithmetic first holds at z_top; that level is used directly.
@@ -575,7 +624,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     unsigned cs_local = 0;
     for (int k = b0; k < b1; ++k) cs_local += S[k];
     unsigned cs_total;
-    unsigned cs = block_exscan(cs_local, ured, &cs_total);  // (synchronises: ztop is final)
+    unsigned cs = block_exscan(cs_local, ured, &cs_total);  // (synchronises: ztop and lhs are final)
     const int z_top = (int)*ztop;
     for (int k = b0; k < b1; ++k) {
       cs += S[k];
