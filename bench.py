@@ -155,6 +155,76 @@ def run_reference(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def batched_leg(torch, hr, local, n_imgs=512, steps=10, warmup=3, seed=3):
+    """The batched form: n mixed-size 8-bit images (areas log-uniform in 320x240 .. 1920x1080, aspect
+    4:3/16:9/3:2) per graph-replayed batch call.  Images are crops of 16 generated 1920x1248 images
+    (the largest 4:3 image of that area is 1663x1247)."""
+    import numpy as np
+    from paper_2510_21100_gb300 import autotune, synth
+    sizes = synth.mixed_batch_sizes(n_imgs, seed)
+    rng = np.random.default_rng(seed)
+    bases = []
+    for i in range(16):
+        lo, hi = synth.illumination_range(seed * 100 + i)
+        bases.append(torch.from_numpy(synth.low_light_image(1920, 1248, seed=synth.seed_for(2, i),
+                                                            illum_lo=lo, illum_hi=hi)).cuda())
+    ins = []
+    for k, (w, h) in enumerate(sizes):
+        b = bases[k % 16]
+        y, x = int(rng.integers(0, 1248 - h + 1)), int(rng.integers(0, 1920 - w + 1))
+        t = hr.aligned_empty(h, w, device=f"cuda:{local}")
+        t.copy_(b[y:y + h, x:x + w])
+        ins.append(t)
+    outs = [hr.aligned_empty(int(t.shape[0]), int(t.shape[1]), device=f"cuda:{local}") for t in ins]
+    ctx = hr.Context(hr.Params(), device=local)
+    tune, _ = autotune.autotune(ctx, ins, outs, reps=2, cache_path=None)
+    mp = sum(w * h for w, h in sizes) / 1e6
+    for _ in range(warmup):
+        ctx.enhance_batch(ins, outs)
+    torch.cuda.synchronize()
+    l0 = ctx.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        ctx.enhance_batch(ins, outs)
+    e1.record()
+    torch.cuda.synchronize()
+    ctx.check()
+    ms = e0.elapsed_time(e1) / steps
+    byts = 3 * 3 * mp * 1e6  # read for the histograms, read + write for the apply
+    return {"workload": f"{n_imgs} mixed uint8 images, {mp:.1f} MP per batch call, K=256, T=10", "images": n_imgs,
+            "MP": mp, "ms_per_batch": ms, "MP_per_s": mp / (ms / 1e3), "tuning": tune,
+            "gpu_launches_per_batch": (ctx.kernel_launches() - l0) / steps, "pipeline_GBps": byts / (ms / 1e3) / 1e9}
+
+
+def precision_leg(torch, hr, local, n_imgs=64, steps=2, warmup=1):
+    """The reduced-precision form: 1000x664 12-bit (uint16) images, K=4096, FP32 solve sums."""
+    from paper_2510_21100_gb300 import synth
+    pool = [torch.from_numpy(synth.low_light_image(1000, 664, seed=synth.seed_for(3, i), bits=12)).cuda()
+            for i in range(8)]
+    ins = []
+    for i in range(n_imgs):
+        t = hr.aligned_empty(664, 1000, dtype=torch.uint16, device=f"cuda:{local}")
+        t.copy_(pool[i % 8])
+        ins.append(t)
+    outs = [hr.aligned_empty(664, 1000, dtype=torch.uint16, device=f"cuda:{local}") for _ in ins]
+    ctx = hr.Context(hr.Params(K=4096, precision=hr.PREC_FP32, stage_timing=False), device=local)
+    for _ in range(warmup):
+        ctx.enhance_batch(ins, outs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        ctx.enhance_batch(ins, outs)
+    e1.record()
+    torch.cuda.synchronize()
+    ctx.check()
+    ms = e0.elapsed_time(e1) / steps
+    mp = 1000 * 664 * n_imgs / 1e6
+    return {"workload": f"{n_imgs} x 1000x664 uint16 (12-bit) images, K=4096, FP32 solve", "images": n_imgs,
+            "ms_per_batch": ms, "MP_per_s": mp / (ms / 1e3)}
+
+
 def timed_loop(ctx, dins, douts, steps, warmup, dist, torch):
     n = len(dins)
     for s in range(warmup):
@@ -285,8 +355,8 @@ def main():
         per = {}
         for (w2, h2) in ((1000, 664), (3840, 2160)):
             ims = make_images(w2, h2)
-            di = [torch.from_numpy(im).cuda() for im in ims]
-            do = [torch.empty_like(d) for d in di]
+            di = [hr.to_device_aligned(im, f"cuda:{local}") for im in ims]
+            do = [hr.aligned_empty(h2, w2, device=f"cuda:{local}") for _ in ims]
             c2 = hr.Context(hr.Params(stage_timing=True), device=local)
             st = max(50, a.steps // 4)
             mt, _, stg = timed_loop(c2, di, do, st, max(3, a.warmup // 2), None, torch)
@@ -297,6 +367,8 @@ def main():
                                  "roofline_frac": rl / ms2}
             c2.close()
         line["per_size"] = per
+        line["batched"] = batched_leg(torch, hr, local)
+        line["precision"] = precision_leg(torch, hr, local)
         rate, reps, shape = cpu_oracle_rate(imgs, seconds=10.0)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{reps} x full {shape[1]}x{shape[0]} image, single-threaded FP64 C oracle"}

@@ -83,6 +83,20 @@ typedef struct {
 
 typedef struct hr_ctx hr_ctx;
 
+/* Launch shapes (not part of the paper's method).  hist_ctas_per_sm, apply_ctas_per_sm: the
+ * persistent grids of the two pixel passes are SMs x this many CTAs (1..32; default 8);
+ * solve_cluster: CTAs per thread-block cluster for a single image's solve (1, 2, 4, 8 or 16;
+ * default 16, lowered automatically when that cluster cannot be resident); use_graph: 1 to
+ * capture enhance_batch's launches into a CUDA graph that is replayed while the batch's geometry
+ * (image count, sizes, element size, alignment) is unchanged (default 1).  Stage timing is not
+ * recorded for graph replays. */
+typedef struct {
+  int hist_ctas_per_sm;
+  int apply_ctas_per_sm;
+  int solve_cluster;
+  int use_graph;
+} hr_tuning;
+
 /* Fills *p with the defaults: K = 256, alpha = beta = 1e-3, gamma = 2.2 (Sec. III.C),
  * eps = 0, max_iter = 10 (Sec. IV.C), FP64, fixed iterations. */
 void histretinex_default_params(hr_params* p);
@@ -102,9 +116,13 @@ hr_status histretinex_enhance(hr_ctx* ctx, const void* d_in, void* d_out, int wi
                               size_t in_pitch, size_t out_pitch, int elem_bytes, void* stream);
 
 /* Enhances n images (each as in histretinex_enhance) with one launch per pipeline stage:
- * persistent kernels walk per-image work queues, so images of mixed sizes share the GPU.
+ * persistent kernels walk per-image work queues, so images of mixed sizes share the GPU; the
+ * launches are captured into a CUDA graph and replayed while the batch geometry is unchanged.
  * The arrays are HOST arrays of length n (d_in[i], d_out[i] are device pointers).
- * Each image's result is identical to what histretinex_enhance returns for it alone. */
+ * Every image is solved by one CTA, so its result (pixels, LUT and FP64 histograms) is
+ * bit-identical whatever else is in the batch, including a batch of one.  Against
+ * histretinex_enhance (which solves one image on a CTA cluster, summing in another order) the
+ * pixels and LUT agree and the FP64 histograms agree to rounding. */
 hr_status histretinex_enhance_batch(hr_ctx* ctx, int n, const void* const* d_in, void* const* d_out,
                                     const int* width, const int* height, const size_t* in_pitch,
                                     const size_t* out_pitch, int elem_bytes, void* stream);
@@ -131,6 +149,14 @@ hr_status histretinex_destroy(hr_ctx* ctx);
 
 /* Static description of a status code. */
 const char* histretinex_status_string(hr_status s);
+
+/* Device workspace bytes the context keeps per image of a batch (for memory budgeting). */
+size_t histretinex_workspace_bytes(const hr_ctx* ctx);
+
+/* Sets / reads the context's launch shapes (see hr_tuning).  Invalid fields give
+ * HR_ERR_INVALID_ARG and leave the tuning unchanged. */
+hr_status histretinex_set_tuning(hr_ctx* ctx, const hr_tuning* t);
+hr_status histretinex_get_tuning(const hr_ctx* ctx, hr_tuning* t);
 
 /* Stage timing (needs HR_FLAG_STAGE_TIMING): every enhance / enhance_batch call records CUDA
  * events on its own stream before and after each of its three stages.  This call waits for

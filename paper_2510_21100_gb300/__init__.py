@@ -23,7 +23,8 @@ EXPORTS = (
     "histretinex_default_params", "histretinex_create", "histretinex_enhance", "histretinex_enhance_batch",
     "histretinex_enhance_host", "histretinex_get_debug", "histretinex_sync_status", "histretinex_destroy",
     "histretinex_status_string", "histretinex_kernel_launches", "histretinex_stage_times",
-    "histretinex_profile_solve",
+    "histretinex_profile_solve", "histretinex_set_tuning", "histretinex_get_tuning",
+    "histretinex_workspace_bytes",
 )
 
 
@@ -37,6 +38,15 @@ class hr_params(ctypes.Structure):
         ("max_iter", ctypes.c_int),
         ("precision", ctypes.c_int),
         ("flags", ctypes.c_uint),
+    ]
+
+
+class hr_tuning(ctypes.Structure):
+    _fields_ = [
+        ("hist_ctas_per_sm", ctypes.c_int),
+        ("apply_ctas_per_sm", ctypes.c_int),
+        ("solve_cluster", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
     ]
 
 
@@ -77,6 +87,12 @@ def _lib():
         L.histretinex_stage_times.restype = ctypes.c_int
         L.histretinex_profile_solve.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(i)]
         L.histretinex_profile_solve.restype = ctypes.c_int
+        L.histretinex_set_tuning.argtypes = [vp, ctypes.POINTER(hr_tuning)]
+        L.histretinex_set_tuning.restype = ctypes.c_int
+        L.histretinex_get_tuning.argtypes = [vp, ctypes.POINTER(hr_tuning)]
+        L.histretinex_get_tuning.restype = ctypes.c_int
+        L.histretinex_workspace_bytes.argtypes = [vp]
+        L.histretinex_workspace_bytes.restype = ctypes.c_size_t
         for name in ("histretinex_create", "histretinex_enhance", "histretinex_enhance_batch",
                      "histretinex_enhance_host", "histretinex_get_debug", "histretinex_sync_status",
                      "histretinex_destroy"):
@@ -113,6 +129,27 @@ class Params:
 def _check(code, what=""):
     if code != OK:
         raise HistRetinexError(code, what)
+
+
+def aligned_empty(H: int, W: int, dtype=None, device="cuda"):
+    """An (H, W, 3) image tensor whose rows start on 16-byte boundaries (the pixel passes' fast
+    path needs that); the row pitch is 3 W rounded up to 16 bytes."""
+    import torch
+    dtype = dtype or torch.uint8
+    eb = torch.empty((), dtype=dtype).element_size()
+    row = (3 * W * eb + 15) // 16 * 16 // eb
+    buf = torch.empty((H, row), dtype=dtype, device=device)
+    return buf.as_strided((H, W, 3), (row, 3, 1))
+
+
+def to_device_aligned(img, device="cuda", stream=None):
+    """Copies a host image (numpy array or CPU tensor, (H, W, 3)) into aligned_empty() storage."""
+    import numpy as np
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(img)) if isinstance(img, np.ndarray) else img
+    out = aligned_empty(t.shape[0], t.shape[1], t.dtype, device)
+    out.copy_(t, non_blocking=True)
+    return out
 
 
 def _stream_ptr(stream):
@@ -248,6 +285,21 @@ class Context:
         calls = ctypes.c_int(0)
         _check(_lib().histretinex_stage_times(self._h, ms, ctypes.byref(calls), int(reset)), "histretinex_stage_times")
         return ms[0], ms[1], ms[2], calls.value
+
+    def workspace_bytes(self) -> int:
+        """Device workspace bytes per image of a batch."""
+        return int(_lib().histretinex_workspace_bytes(self._h))
+
+    def tuning(self) -> dict:
+        t = hr_tuning()
+        _check(_lib().histretinex_get_tuning(self._h, ctypes.byref(t)), "histretinex_get_tuning")
+        return {k: getattr(t, k) for k, _ in hr_tuning._fields_}
+
+    def set_tuning(self, **kw):
+        cur = self.tuning()
+        cur.update(kw)
+        t = hr_tuning(**cur)
+        _check(_lib().histretinex_set_tuning(self._h, ctypes.byref(t)), "histretinex_set_tuning")
 
     def profile_solve(self, image: int = 0):
         """Solve-phase timestamps (ns) of the last call (needs Params(debug=True))."""

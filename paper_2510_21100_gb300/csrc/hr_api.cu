@@ -39,6 +39,11 @@ struct hr_ctx {
   int ev_next = 0;
   double stage_ms[3] = {0, 0, 0};
   int stage_calls = 0;
+  hr_tuning tune{8, 8, 16, 1};
+  // captured batch pipeline and the geometry it was captured for
+  cudaGraphExec_t graph = nullptr;
+  int g_n = 0, g_total = 0, g_eb = 0, g_fast_in = 0, g_fast_out = 0;
+  hr_tuning g_tune{0, 0, 0, 0};
 };
 
 namespace hr {
@@ -140,8 +145,13 @@ void build_jstart1(int K, double gamma, std::vector<uint16_t>& t) {
   }
 }
 
+void drop_graph(hr_ctx* c) {  // a captured pipeline holds workspace and descriptor pointers
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+}
+
 hr_status ensure_slots(hr_ctx* c, int n) {
   if (n <= c->n_slots) return HR_OK;
+  drop_graph(c);
   if (c->d_slots) { cudaFree(c->d_slots); c->d_slots = nullptr; c->n_slots = 0; }
   HR_CUDA(cudaMalloc(&c->d_slots, c->lay.bytes * (size_t)n));
   c->n_slots = n;
@@ -150,6 +160,7 @@ hr_status ensure_slots(hr_ctx* c, int n) {
 
 hr_status ensure_desc(hr_ctx* c, int n) {
   if (n <= c->cap_imgs) return HR_OK;
+  drop_graph(c);
   if (c->desc_done) HR_CUDA(cudaEventSynchronize(c->desc_done));
   cudaFree(c->d_imgs); cudaFree(c->d_tile_start); cudaFreeHost(c->h_imgs); cudaFreeHost(c->h_tile_start);
   c->d_imgs = nullptr; c->d_tile_start = nullptr; c->h_imgs = nullptr; c->h_tile_start = nullptr; c->cap_imgs = 0;
@@ -185,11 +196,49 @@ hr_status fold_timing(hr_ctx* c, int i) {
   return HR_OK;
 }
 
-hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, cudaStream_t st) {
+// The pipeline's device work on one stream: zero the histograms, histogram pass, solve, apply.
+// ev (optional): four events recorded around the three stages.
+cudaError_t enqueue_stages(hr_ctx* c, int n, int total, int elem_bytes, bool fast_in, bool fast_out, bool batched,
+                           cudaStream_t st, cudaEvent_t* ev) {
+  const int K = c->p.K;
+  cudaError_t e;
+  // zero H_C(S) and H_C(grad S) of every slot used (S and G are adjacent at the slot start)
+  e = cudaMemset2DAsync(c->d_slots + c->lay.S, c->lay.bytes, 0, (size_t)2 * K * sizeof(unsigned), (size_t)n, st);
+  if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
+  e = hr::launch_hist(c->d_imgs, n, c->d_tile_start, total, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay,
+                      c->d_status, c->sm_count * c->tune.hist_ctas_per_sm, st, fast_in);
+  if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
+  hr::SolveArgs a{};
+  a.K = K;
+  a.alpha = c->p.alpha;
+  a.beta = c->p.beta;
+  a.eps = c->p.eps;
+  a.max_iter = c->p.max_iter;
+  a.fixed_iters = (c->p.flags & HR_FLAG_FIXED_ITERS) ? 1 : 0;
+  a.jstart1 = c->d_jstart1;
+  a.slots = c->d_slots;
+  a.slot_bytes = c->lay.bytes;
+  a.lay = c->lay;
+  a.status = c->d_status;
+  a.vec_in_smem = K <= 1024 ? 1 : 0;
+  a.profile = (c->p.flags & HR_FLAG_DEBUG_OUT) ? 1 : 0;
+  a.fp32 = c->p.precision == HR_PREC_FP32 ? 1 : 0;
+  e = hr::launch_solve(a, n, batched ? 1 : c->tune.solve_cluster, st);
+  if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
+  e = hr::launch_apply(c->d_imgs, n, c->d_tile_start, total, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay,
+                       c->d_status, c->sm_count * c->tune.apply_ctas_per_sm, st, fast_out);
+  if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, cudaStream_t st, bool batched) {
   const int K = c->p.K;
   if (elem_bytes != 1 && elem_bytes != 2) return HR_ERR_INVALID_ARG;
   if (elem_bytes == 1 && K > 256) return HR_ERR_INVALID_ARG;
-  if (c->p.precision != HR_PREC_FP64) return HR_ERR_UNSUPPORTED;
   long long total = 0;
   for (int i = 0; i < n; ++i) {
     const ImageDesc& d = imgs[i];
@@ -228,10 +277,35 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
     HR_CUDA(cudaEventRecord(c->desc_done, st));
     c->last_imgs.assign(imgs, imgs + n);
   }
-  // zero H_C(S) and H_C(grad S) of every slot used (S and G are adjacent at the slot start)
-  HR_CUDA(cudaMemset2DAsync(c->d_slots + c->lay.S, c->lay.bytes, 0, (size_t)2 * K * sizeof(unsigned), (size_t)n, st));
-  const int px_grid = c->sm_count * 8;
   const bool timing = (c->p.flags & HR_FLAG_STAGE_TIMING) != 0;
+  const bool graph = batched && c->tune.use_graph && n > 1 && !timing;
+  if (graph) {
+    const bool same = c->graph && c->g_n == n && c->g_total == (int)total && c->g_eb == elem_bytes &&
+                      c->g_fast_in == (int)fast_in && c->g_fast_out == (int)fast_out &&
+                      std::memcmp(&c->g_tune, &c->tune, sizeof(hr_tuning)) == 0;
+    if (!same) {
+      drop_graph(c);
+      cudaStream_t cap;
+      HR_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        e = enqueue_stages(c, n, (int)total, elem_bytes, fast_in, fast_out, batched, cap, nullptr);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (e == cudaSuccess) e = e2;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);
+      if (g) cudaGraphDestroy(g);
+      cudaStreamDestroy(cap);
+      if (e != cudaSuccess) { c->graph = nullptr; return cuda_fail(e); }
+      c->g_n = n; c->g_total = (int)total; c->g_eb = elem_bytes;
+      c->g_fast_in = (int)fast_in; c->g_fast_out = (int)fast_out; c->g_tune = c->tune;
+    }
+    HR_CUDA(cudaGraphLaunch(c->graph, st));
+    c->launches += 3;
+    c->last_n = n;
+    return HR_OK;
+  }
   cudaEvent_t* ev = nullptr;
   if (timing) {
     const int i = c->ev_next;
@@ -242,30 +316,8 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
       for (int q = 0; q < 4; ++q) HR_CUDA(cudaEventCreate(&c->ev[i][q]));
     ev = c->ev[i];
     c->ev_used[i] = true;
-    HR_CUDA(cudaEventRecord(ev[0], st));
   }
-  HR_CUDA(hr::launch_hist(c->d_imgs, n, c->d_tile_start, (int)total, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay,
-                          c->d_status, px_grid, st, fast_in));
-  if (ev) HR_CUDA(cudaEventRecord(ev[1], st));
-  hr::SolveArgs a{};
-  a.K = K;
-  a.alpha = c->p.alpha;
-  a.beta = c->p.beta;
-  a.eps = c->p.eps;
-  a.max_iter = c->p.max_iter;
-  a.fixed_iters = (c->p.flags & HR_FLAG_FIXED_ITERS) ? 1 : 0;
-  a.jstart1 = c->d_jstart1;
-  a.slots = c->d_slots;
-  a.slot_bytes = c->lay.bytes;
-  a.lay = c->lay;
-  a.status = c->d_status;
-  a.vec_in_smem = K <= 1024 ? 1 : 0;
-  a.profile = (c->p.flags & HR_FLAG_DEBUG_OUT) ? 1 : 0;
-  HR_CUDA(hr::launch_solve(a, n, st));
-  if (ev) HR_CUDA(cudaEventRecord(ev[2], st));
-  HR_CUDA(hr::launch_apply(c->d_imgs, n, c->d_tile_start, (int)total, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay,
-                           c->d_status, px_grid, st, fast_out));
-  if (ev) HR_CUDA(cudaEventRecord(ev[3], st));
+  HR_CUDA(enqueue_stages(c, n, (int)total, elem_bytes, fast_in, fast_out, batched, st, ev));
   c->launches += 3;
   c->last_n = n;
   return HR_OK;
@@ -323,7 +375,7 @@ hr_status histretinex_enhance(hr_ctx* c, const void* d_in, void* d_out, int widt
   ImageDesc d{static_cast<const uint8_t*>(d_in), static_cast<uint8_t*>(d_out), width, height, (long long)in_pitch,
               (long long)out_pitch};
   HR_CUDA(cudaSetDevice(c->device));
-  return run_pipeline(c, 1, &d, elem_bytes, static_cast<cudaStream_t>(stream));
+  return run_pipeline(c, 1, &d, elem_bytes, static_cast<cudaStream_t>(stream), false);
 }
 
 hr_status histretinex_enhance_batch(hr_ctx* c, int n, const void* const* d_in, void* const* d_out, const int* width,
@@ -335,7 +387,7 @@ hr_status histretinex_enhance_batch(hr_ctx* c, int n, const void* const* d_in, v
     v[i] = ImageDesc{static_cast<const uint8_t*>(d_in[i]), static_cast<uint8_t*>(d_out[i]), width[i], height[i],
                      (long long)in_pitch[i], (long long)out_pitch[i]};
   HR_CUDA(cudaSetDevice(c->device));
-  return run_pipeline(c, n, v.data(), elem_bytes, static_cast<cudaStream_t>(stream));
+  return run_pipeline(c, n, v.data(), elem_bytes, static_cast<cudaStream_t>(stream), true);
 }
 
 hr_status histretinex_enhance_host(hr_ctx* c, const void* h_in, void* h_out, int width, int height, size_t in_pitch,
@@ -344,7 +396,8 @@ hr_status histretinex_enhance_host(hr_ctx* c, const void* h_in, void* h_out, int
     return HR_ERR_INVALID_ARG;
   const size_t row = (size_t)3 * width * elem_bytes;
   if (in_pitch < row || out_pitch < row) return HR_ERR_INVALID_ARG;
-  const size_t bytes = row * (size_t)height;
+  const size_t dpitch = (row + 15) / 16 * 16;  // 16-byte aligned device rows: the fast pixel paths
+  const size_t bytes = dpitch * (size_t)height;
   HR_CUDA(cudaSetDevice(c->device));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (bytes > c->io_bytes) {
@@ -355,12 +408,12 @@ hr_status histretinex_enhance_host(hr_ctx* c, const void* h_in, void* h_out, int
     HR_CUDA(cudaMalloc(&c->d_io_out, bytes));
     c->io_bytes = bytes;
   }
-  HR_CUDA(cudaMemcpy2DAsync(c->d_io_in, row, h_in, in_pitch, row, (size_t)height, cudaMemcpyHostToDevice, st));
+  HR_CUDA(cudaMemcpy2DAsync(c->d_io_in, dpitch, h_in, in_pitch, row, (size_t)height, cudaMemcpyHostToDevice, st));
   ImageDesc d{static_cast<const uint8_t*>(c->d_io_in), static_cast<uint8_t*>(c->d_io_out), width, height,
-              (long long)row, (long long)row};
-  hr_status s = run_pipeline(c, 1, &d, elem_bytes, st);
+              (long long)dpitch, (long long)dpitch};
+  hr_status s = run_pipeline(c, 1, &d, elem_bytes, st, false);
   if (s != HR_OK) return s;
-  HR_CUDA(cudaMemcpy2DAsync(h_out, out_pitch, c->d_io_out, row, row, (size_t)height, cudaMemcpyDeviceToHost, st));
+  HR_CUDA(cudaMemcpy2DAsync(h_out, out_pitch, c->d_io_out, dpitch, row, (size_t)height, cudaMemcpyDeviceToHost, st));
   return histretinex_sync_status(c, stream);
 }
 
@@ -435,6 +488,7 @@ hr_status histretinex_destroy(hr_ctx* c) {
   cudaFreeHost(c->h_tile_start);
   cudaFree(c->d_io_in);
   cudaFree(c->d_io_out);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->desc_done) cudaEventDestroy(c->desc_done);
   for (int i = 0; i < hr_ctx::kRing; ++i)
     for (int q = 0; q < 4; ++q)
@@ -454,6 +508,25 @@ const char* histretinex_status_string(hr_status s) {
     case HR_ERR_TIMEOUT: return "device wait timed out";
   }
   return "unknown status";
+}
+
+size_t histretinex_workspace_bytes(const hr_ctx* c) { return c ? c->lay.bytes : 0; }
+
+hr_status histretinex_set_tuning(hr_ctx* c, const hr_tuning* t) {
+  if (!c || !t) return HR_ERR_INVALID_ARG;
+  if (t->hist_ctas_per_sm < 1 || t->hist_ctas_per_sm > 32 || t->apply_ctas_per_sm < 1 || t->apply_ctas_per_sm > 32)
+    return HR_ERR_INVALID_ARG;
+  if (t->solve_cluster < 1 || t->solve_cluster > 16 || (t->solve_cluster & (t->solve_cluster - 1)))
+    return HR_ERR_INVALID_ARG;
+  if (t->use_graph != 0 && t->use_graph != 1) return HR_ERR_INVALID_ARG;
+  c->tune = *t;
+  return HR_OK;
+}
+
+hr_status histretinex_get_tuning(const hr_ctx* c, hr_tuning* t) {
+  if (!c || !t) return HR_ERR_INVALID_ARG;
+  *t = c->tune;
+  return HR_OK;
 }
 
 hr_status histretinex_stage_times(hr_ctx* c, double* ms, int* calls, int reset) {

@@ -63,17 +63,18 @@ struct SolveArgs {
   unsigned* status;
   int vec_in_smem;           // 1: solver vectors in dynamic shared memory
   int profile;               // 1: record phase timestamps into the slot's misc area
+  int fp32;                  // 1: solve sums in FP32 (reduced-precision form), else FP64
 };
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_hist(const ImageDesc* d_imgs, int n, const int* d_tile_start, int total_tiles, int elem_bytes,
                         int K, uint8_t* slots, size_t slot_bytes, SlotLayout lay, unsigned* status,
                         int grid, cudaStream_t st, bool fast);
-cudaError_t launch_solve(const SolveArgs& a, int n, cudaStream_t st);
+cudaError_t launch_solve(const SolveArgs& a, int n, int cluster, cudaStream_t st);
 cudaError_t launch_apply(const ImageDesc* d_imgs, int n, const int* d_tile_start, int total_tiles, int elem_bytes,
                          int K, uint8_t* slots, size_t slot_bytes, SlotLayout lay, unsigned* status, int grid,
                          cudaStream_t st, bool fast);
-size_t solve_smem_bytes(int K, int vec_in_smem);
+size_t solve_smem_bytes(int K, int vec_in_smem, size_t fsize);
 
 // Geometry of the pixel passes: tiles of kTileW x kTileH pixels.
 constexpr int kTileW = 128;

@@ -45,6 +45,10 @@ __device__ __forceinline__ double rcp64(double d) {
   return fma(r, e, r);
 }
 
+// 1/d in the solver's arithmetic: FP64 (plain form) or FP32 (reduced-precision form).
+__device__ __forceinline__ double rcpF(double d) { return rcp64(d); }
+__device__ __forceinline__ float rcpF(float d) { return __frcp_rn(d); }
+
 // index(i, j) = floor((2 i j + K - 1) / (2 (K - 1))): nearest level to i j / (K - 1).
 // The quotient is < K <= 4096, so a float estimate is within one of it.
 __device__ __forceinline__ int class_index(int i, int j, int km1, float inv_d) {
@@ -129,10 +133,10 @@ __device__ unsigned block_count(int n, F f, unsigned* red) {
 }
 
 // Sum over the lanes of one warp (lane-strided, then a fixed shuffle tree); used from lane 0.
-template <class F>
-__device__ __forceinline__ double warp_sum(int n, F f) {
+template <class Fn>
+__device__ __forceinline__ auto warp_sum(int n, Fn f) -> decltype(f(0)) {
   const int l = threadIdx.x & 31;
-  double s = 0.0;
+  decltype(f(0)) s = 0;
   for (int i = l; i < n; i += 32) s += f(i);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
   return s;
@@ -181,15 +185,15 @@ struct ClassPlan {
   unsigned cell0;      // first own cell (global class-major index)
   unsigned* listp;     // own cells, indexed by (cell - cell0)
   uint2* piecep;       // own pieces, indexed by (piece - pA)
-  double* partp;       // own piece sums, indexed by (piece - pbase)
+  void* partp;         // own piece sums (solver arithmetic type), indexed by (piece - pbase)
   unsigned pbase;      // pA for shared-memory buffers, 0 for the global workspace
 };
 
 // Own cell list, pieces and piece sums: shared-memory buffers when they fit, else the global
 // workspace (same indexing either way).
 struct OwnBufs {
-  unsigned* s_list; uint2* s_piece; double* s_part;   // shared memory
-  unsigned* g_list; uint2* g_piece; double* g_part;   // global workspace
+  unsigned* s_list; uint2* s_piece; void* s_part;   // shared memory
+  unsigned* g_list; uint2* g_piece; void* g_part;   // global workspace
 };
 
 template <class JS, class CL>
@@ -268,28 +272,29 @@ __device__ ClassPlan plan_classes(const cg::cluster_group& cl, int nR, int ncls,
 
 // Sums the own pieces into the piece sums, then each own class's pieces; emit(c, total).
 // Small classes are summed by one lane, larger ones by a warp (strided sums + shuffle tree).
-template <class EMIT>
-__device__ void class_totals(const ClassPlan& P, const unsigned* csz, const unsigned* pst, const double* Rc,
-                             const double* Lc, EMIT emit) {
+template <typename F, class EMIT>
+__device__ void class_totals(const ClassPlan& P, const unsigned* csz, const unsigned* pst, const F* Rc, const F* Lc,
+                             EMIT emit) {
+  F* part = static_cast<F*>(P.partp);
   const unsigned pbase = P.pbase;
   for (unsigned p = P.pA + threadIdx.x; p < P.pB; p += NT) {
     const uint2 pc = P.piecep[p - pbase];
     const unsigned len = pc.y & 0xffffu;
     const unsigned* cells = P.listp + pc.x;
-    double acc = 0.0;
+    F acc = 0;
     for (unsigned c = 0; c < len; ++c) {
       const unsigned cell = cells[c];
       acc = fma(Rc[cell >> 16], Lc[cell & 0xffffu], acc);
     }
-    P.partp[p - pbase] = acc;
+    part[p - pbase] = acc;
   }
   __syncthreads();
   constexpr unsigned kSmall = 4;
   for (int c = P.cA + threadIdx.x; c < P.cB; c += NT) {
     const unsigned np = (csz[c] + kPiece - 1) / kPiece;
     if (np > kSmall) continue;
-    const double* ps = P.partp + (pst[c] - pbase);
-    double s = 0.0;
+    const F* ps = part + (pst[c] - pbase);
+    F s = 0;
     for (unsigned p = 0; p < np; ++p) s += ps[p];
     emit(c, s);
   }
@@ -297,21 +302,23 @@ __device__ void class_totals(const ClassPlan& P, const unsigned* csz, const unsi
   for (int c = P.cA + w; c < P.cB; c += NW) {
     const unsigned np = (csz[c] + kPiece - 1) / kPiece;
     if (np <= kSmall) continue;
-    const double* ps = P.partp + (pst[c] - pbase);
-    double s = 0.0;
+    const F* ps = part + (pst[c] - pbase);
+    F s = 0;
     for (unsigned p = l; p < np; p += 32) s += ps[p];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
     if (l == 0) emit(c, s);
   }
 }
 
+template <typename F>
 __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double conv[2][NW];
+  __shared__ F conv[2][NW];
   const cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   const int K = A.K;
+  const F alpha = (F)A.alpha, beta = (F)A.beta, eps = (F)A.eps;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t* slot = A.slots + (size_t)(blockIdx.x / C) * A.slot_bytes;
   const SlotLayout& lay = A.lay;
@@ -338,25 +345,25 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   unsigned* csz = reinterpret_cast<unsigned*>(smem + off); off += (size_t)K * 4;
   unsigned* cst = reinterpret_cast<unsigned*>(smem + off); off += (size_t)K * 4;
   unsigned* pst = reinterpret_cast<unsigned*>(smem + off); off += (size_t)K * 4;
-  double* scal = reinterpret_cast<double*>(smem + off); off += 8 * sizeof(double);  // per-iteration scalars
+  F* scal = reinterpret_cast<F*>(smem + off); off += 8 * sizeof(double);  // per-iteration scalars
   unsigned* ured = reinterpret_cast<unsigned*>(smem + off); off += ((NW + 2) * sizeof(unsigned) + 15) & ~(size_t)15;
   double* scr = reinterpret_cast<double*>(smem + off); off += NT * sizeof(double);   // LUT scans
   OwnBufs ob;
-  ob.s_part = reinterpret_cast<double*>(smem + off); off += (size_t)kPieceCap * sizeof(double);
+  ob.s_part = smem + off; off += (size_t)kPieceCap * sizeof(F);
   ob.s_piece = reinterpret_cast<uint2*>(smem + off); off += (size_t)kPieceCap * sizeof(uint2);
   ob.s_list = reinterpret_cast<unsigned*>(smem + off); off += (size_t)kListCap * sizeof(unsigned);
   ob.g_list = reinterpret_cast<unsigned*>(slot + lay.list);
   ob.g_piece = reinterpret_cast<uint2*>(slot + lay.piece);
-  ob.g_part = reinterpret_cast<double*>(slot + lay.part);
-  double* vec = A.vec_in_smem ? reinterpret_cast<double*>(smem + off) : reinterpret_cast<double*>(slot + lay.vec);
-  double* Rc = vec;           // H_C(R) on supp G (compacted)
-  double* Lc = vec + K;       // H_C(L) on supp S (compacted)
-  double* L2c = vec + 2 * K;  // L^2 (compacted); column sums of Eq. 12; the enhanced histogram at the end
-  double* RRc = vec + 3 * K;  // R' R (compacted)
-  double* Ru = vec + 4 * K;   // Eq. 13 before Eq. 15
-  double* Lu = vec + 5 * K;   // Eq. 12 before Eq. 14
-  double* q = vec + 6 * K;    // S_k / P_k (level-indexed)
-  double* Sd = vec + 7 * K;   // S as double (level-indexed)
+  ob.g_part = slot + lay.part;
+  F* vec = A.vec_in_smem ? reinterpret_cast<F*>(smem + off) : reinterpret_cast<F*>(slot + lay.vec);
+  F* Rc = vec;           // H_C(R) on supp G (compacted)
+  F* Lc = vec + K;       // H_C(L) on supp S (compacted)
+  F* L2c = vec + 2 * K;  // L^2 (compacted); column sums of Eq. 12; the enhanced histogram at the end
+  F* RRc = vec + 3 * K;  // R' R (compacted)
+  F* Ru = vec + 4 * K;   // Eq. 13 before Eq. 15
+  F* Lu = vec + 5 * K;   // Eq. 12 before Eq. 14
+  F* q = vec + 6 * K;    // S_k / P_k (level-indexed)
+  F* Sd = vec + 7 * K;   // S as F (level-indexed)
 
   // ---- supports and N (every CTA) -------------------------------------------------------------
   const int per = iceil_div(K, NT);
@@ -371,15 +378,15 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     if (G[k] > 0u) RI[offR++] = (uint16_t)k;
     posL[k] = (uint16_t)offL;
     if (S[k] > 0u) LJ[offL++] = (uint16_t)k;
-    Sd[k] = (double)S[k];
+    Sd[k] = (F)S[k];
     q[k] = 0.0;
   }
   if (tid == 0) posL[K] = (uint16_t)nLu;
   __syncthreads();
   const int nR = (int)nRu, nL = (int)nLu;
-  const double N = (double)Nu;
-  const double invN = rcp64(N);
-  const double invNN = rcp64(N * N);
+  const F N = (F)Nu;
+  const F invN = rcpF(N);
+  const F invNN = rcpF(N * N);
   const int km1 = K - 1;
   const float inv_d = 1.0f / (float)(2 * km1);
 
@@ -396,38 +403,38 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   const int GB = C == 1 ? 4 : 32;   // lanes per column in the Eq. 12 sums
   // (one image's arithmetic depends on C only through these group sizes and the class split)
 
-  for (int a = tid; a < nR; a += NT) Rc[a] = (double)G[RI[a]];   // R^(0) = H_C(grad S)
-  for (int b = tid; b < nL; b += NT) Lc[b] = (double)S[LJ[b]];   // L^(0) = H_C(S)
+  for (int a = tid; a < nR; a += NT) Rc[a] = (F)G[RI[a]];   // R^(0) = H_C(grad S)
+  for (int b = tid; b < nL; b += NT) Lc[b] = (F)S[LJ[b]];   // L^(0) = H_C(S)
   __syncthreads();
 
   // R = scR * R0 and L = scL * L0: the renormalisation of Eq. 15 / Eq. 14 is carried as two scales
   // into the next iteration (computed while its class totals run) instead of a separate pass.
-  double* R0 = Rc;
-  double* L0 = Lc;
-  double* R1 = Ru;
-  double* L1 = Lu;
-  double scR = 1.0, scL = 1.0;  // R^(0) = H_C(grad S) and L^(0) = H_C(S) already have mass N
+  F* R0 = Rc;
+  F* L0 = Lc;
+  F* R1 = Ru;
+  F* L1 = Lu;
+  F scR = 1.0, scL = 1.0;  // R^(0) = H_C(grad S) and L^(0) = H_C(S) already have mass N
   int it = 0;
   while (it < A.max_iter) {
     // Eq. 11: class totals P_k of the own classes; q_k = S_k / P_k to every CTA.
     if (warp == NW - 1) {  // meanwhile: the L scale and 1 / denominator of Eq. 13 (every CTA alike)
-      double s1 = 0.0, s2 = 0.0;
-      for (int b = lane; b < nL; b += 32) { const double x = L0[b]; s1 += x; s2 = fma(x, x, s2); }
+      F s1 = 0.0, s2 = 0.0;
+      for (int b = lane; b < nL; b += 32) { const F x = L0[b]; s1 += x; s2 = fma(x, x, s2); }
       for (int o = 16; o > 0; o >>= 1) {
         s1 += __shfl_xor_sync(FULL, s1, o);
         s2 += __shfl_xor_sync(FULL, s2, o);
       }
       if (lane == 0) {
-        const double sl = it == 0 ? 1.0 : N * rcp64(s1);
+        const F sl = it == 0 ? 1.0 : N * rcpF(s1);
         scal[3] = sl;
-        scal[0] = rcp64(fma(s2 * (sl * sl), invNN, A.beta));
+        scal[0] = rcpF(fma(s2 * (sl * sl), invNN, beta));
       }
     }
-    for (int b = tid; b < nL; b += NT) { const double x = L0[b]; L2c[b] = x * x; }
-    class_totals(PP, csz, pst, R0, L0, [&](int c, double Pu) {  // (after a barrier: scal[3] is set)
+    for (int b = tid; b < nL; b += NT) { const F x = L0[b]; L2c[b] = x * x; }
+    class_totals<F>(PP, csz, pst, R0, L0, [&](int c, F Pu) {  // (after a barrier: scal[3] is set)
       const int k = LJ[c];
-      const double P = Pu * (scR * scal[3]);
-      q[k] = P > 0.0 ? Sd[k] * rcp64(P) : 0.0;
+      const F P = Pu * (scR * scal[3]);
+      q[k] = P > 0.0 ? Sd[k] * rcpF(P) : 0.0;
     });
     __syncthreads();
     push_mapped(cl, q, LJ, PP.cA, PP.cB, C, rank);
@@ -437,19 +444,19 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
 
     // Eq. 13 for the own rows: lane groups of GA over the illumination bins.
     {
-      const double rdR = scal[0], sl2 = scL * scL;
+      const F rdR = scal[0], sl2 = scL * scL;
       const int gi = lane / GA, gl = lane % GA, rpw = 32 / GA;
       for (int a0 = aA + warp * rpw; a0 < aB; a0 += NW * rpw) {
         const int a = a0 + gi;
-        double acc = 0.0;
+        F acc = 0.0;
         if (a < aB) {
           const int i = RI[a];
           for (int b = gl; b < nL; b += GA) acc = fma(L2c[b], q[class_index(i, LJ[b], km1, inv_d)], acc);
         }
         for (int o = GA >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
         if (gl == 0 && a < aB) {
-          const double r = scR * R0[a];
-          const double ru = fma(r * invN, acc * sl2, A.beta * (double)G[RI[a]]) * rdR;
+          const F r = scR * R0[a];
+          const F ru = fma(r * invN, acc * sl2, beta * (F)G[RI[a]]) * rdR;
           R1[a] = ru;
           RRc[a] = ru * r;
         }
@@ -463,20 +470,20 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
 
     // Eq. 12 for the own columns: lane groups of GB over the reflectance bins.
     if (warp == NW - 1) {  // meanwhile: 1 / denominator of Eq. 12 and the next R scale N / sum R'
-      double s1 = 0.0, s2 = 0.0;
-      for (int a = lane; a < nR; a += 32) { const double x = R1[a]; s1 += x; s2 = fma(x, x, s2); }
+      F s1 = 0.0, s2 = 0.0;
+      for (int a = lane; a < nR; a += 32) { const F x = R1[a]; s1 += x; s2 = fma(x, x, s2); }
       for (int o = 16; o > 0; o >>= 1) {
         s1 += __shfl_xor_sync(FULL, s1, o);
         s2 += __shfl_xor_sync(FULL, s2, o);
       }
-      if (lane == 0) { scal[1] = rcp64(fma(s2, invNN, A.alpha)); scal[2] = N * rcp64(s1); }
+      if (lane == 0) { scal[1] = rcpF(fma(s2, invNN, alpha)); scal[2] = N * rcpF(s1); }
     }
     {
-      double* Bs = L2c;  // column sums (L^2 is not needed again in this iteration)
+      F* Bs = L2c;  // column sums (L^2 is not needed again in this iteration)
       const int gi = lane / GB, gl = lane % GB, cpw = 32 / GB;
       for (int b0 = bA + warp * cpw; b0 < bB; b0 += NW * cpw) {
         const int b = b0 + gi;
-        double acc = 0.0;
+        F acc = 0.0;
         if (b < bB) {
           const int j = LJ[b];
           for (int a = gl; a < nR; a += GB) acc = fma(RRc[a], q[class_index(RI[a], j, km1, inv_d)], acc);
@@ -485,39 +492,39 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         if (gl == 0 && b < bB) Bs[b] = acc;
       }
       __syncthreads();
-      const double rdL = scal[1];
-      for (int b = bA + tid; b < bB; b += NT) L1[b] = fma(scL * L0[b] * invN, Bs[b], A.alpha * Sd[LJ[b]]) * rdL;
+      const F rdL = scal[1];
+      for (int b = bA + tid; b < bB; b += NT) L1[b] = fma(scL * L0[b] * invN, Bs[b], alpha * Sd[LJ[b]]) * rdL;
     }
     __syncthreads();
     push_slice(cl, L1, bA, bB, C, rank);
     cl.sync();
     if (it == 0) stamp();
 
-    const double scR1 = scal[2];
+    const F scR1 = scal[2];
     ++it;
     bool done = false;
     if (!A.fixed_iters) {
       // squared changes of the renormalised histograms (identical data and order in every CTA)
       if (warp == 0) {
-        const double s1 = warp_sum(nL, [&](int b) { return L1[b]; });
-        if (lane == 0) scal[4] = N * rcp64(s1);
+        const F s1 = warp_sum(nL, [&](int b) { return L1[b]; });
+        if (lane == 0) scal[4] = N * rcpF(s1);
       }
       __syncthreads();
-      const double scL1 = scal[4];
-      double dr = 0.0, dl = 0.0;
-      for (int a = tid; a < nR; a += NT) { const double d = scR1 * R1[a] - scR * R0[a]; dr = fma(d, d, dr); }
-      for (int b = tid; b < nL; b += NT) { const double d = scL1 * L1[b] - scL * L0[b]; dl = fma(d, d, dl); }
+      const F scL1 = scal[4];
+      F dr = 0.0, dl = 0.0;
+      for (int a = tid; a < nR; a += NT) { const F d = scR1 * R1[a] - scR * R0[a]; dr = fma(d, d, dr); }
+      for (int b = tid; b < nL; b += NT) { const F d = scL1 * L1[b] - scL * L0[b]; dl = fma(d, d, dl); }
       for (int o = 16; o > 0; o >>= 1) {
         dr += __shfl_xor_sync(FULL, dr, o);
         dl += __shfl_xor_sync(FULL, dl, o);
       }
       if (lane == 0) { conv[0][warp] = dr; conv[1][warp] = dl; }
       __syncthreads();
-      double DR = 0.0, DL = 0.0;
+      F DR = 0.0, DL = 0.0;
       for (int w2 = 0; w2 < NW; ++w2) { DR += conv[0][w2]; DL += conv[1][w2]; }
-      done = DR <= A.eps && DL <= A.eps;
+      done = DR <= eps && DL <= eps;
     }
-    double* t = R0; R0 = R1; R1 = t;
+    F* t = R0; R0 = R1; R1 = t;
     t = L0; L0 = L1; L1 = t;
     scR = scR1;
     __syncthreads();
@@ -526,12 +533,12 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   }
   // renormalised results of Algorithm 1 (Eq. 15 and Eq. 14 applied to the last iterate)
   if (warp == 0) {
-    const double s1 = warp_sum(nL, [&](int b) { return L0[b]; });
-    if (lane == 0) scal[4] = N * rcp64(s1);
+    const F s1 = warp_sum(nL, [&](int b) { return L0[b]; });
+    if (lane == 0) scal[4] = N * rcpF(s1);
   }
   __syncthreads();
   {
-    const double sl = scal[4];
+    const F sl = scal[4];
     for (int a = tid; a < nR; a += NT) R1[a] = scR * R0[a];
     for (int b = tid; b < nL; b += NT) L1[b] = sl * L0[b];
   }
@@ -540,12 +547,12 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   Lc = L1;
 
   // ---- Eq. 17-20: enhanced histogram through the index_1 class map -----------------------------
-  double* T = L2c;  // level-indexed target, filled by every CTA's own classes
+  F* T = L2c;  // level-indexed target, filled by every CTA's own classes
   for (int k = tid; k < K; k += NT) T[k] = 0.0;
   const ClassPlan PT = plan_classes(cl, nR, K, RI, posL, JsTable{A.jstart1, K}, [](int c) { return c; }, csz, cst,
                                     pst, ob, ured, rank, C);  // (its cluster barrier orders the zeroing)
   stamp();
-  class_totals(PT, csz, pst, Rc, Lc, [&](int c, double s) { T[c] = s * invN; });  // count matrix carries 1/N (Eq. 6)
+  class_totals<F>(PT, csz, pst, Rc, Lc, [&](int c, F s) { T[c] = s * invN; });  // count matrix carries 1/N (Eq. 6)
   __syncthreads();
   push_slice(cl, T, PT.cA, PT.cB, C, rank);
   cl.sync();
@@ -554,11 +561,11 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
 
   // ---- histogram matching LUT (rank 0) -----------------------------------------------------------
   {
-    double* CT = RRc;                                                 // inclusive prefix sums of T
-    unsigned long long* lhs = reinterpret_cast<unsigned long long*>(q);  // CT(z) N, made monotone
+    double* CT = reinterpret_cast<double*>(RRc);                      // inclusive prefix sums of T (FP64)
+    unsigned long long* lhs = reinterpret_cast<unsigned long long*>(q);  // CT(z) N, made monotone (FP64 bits)
     const int b0 = k0, b1 = k1;
     double s = 0.0;
-    for (int k = b0; k < b1; ++k) { s += T[k]; CT[k] = s; }
+    for (int k = b0; k < b1; ++k) { s += (double)T[k]; CT[k] = s; }
     double x = s;  // inclusive scan of the per-thread chunk sums: within the warp, then over warps
     for (int o = 1; o < 32; o <<= 1) {
       const double y = __shfl_up_sync(FULL, x, o);
@@ -585,7 +592,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     // first z with lhs(z) >= rhs(s) is found by binary search
     unsigned long long m = 0;
     for (int k = b0; k < b1; ++k) {
-      const unsigned long long v = (unsigned long long)__double_as_longlong(CT[k] * N);
+      const unsigned long long v = (unsigned long long)__double_as_longlong(CT[k] * (double)Nu);
       m = v > m ? v : m;
       lhs[k] = m;
     }
@@ -641,30 +648,30 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   __syncthreads();
 
   // ---- results (level-indexed) -------------------------------------------------------------------
-  for (int k = tid; k < K; k += NT) { Rout[k] = 0.0; Lout[k] = 0.0; Tout[k] = T[k]; }
+  for (int k = tid; k < K; k += NT) { Rout[k] = 0.0; Lout[k] = 0.0; Tout[k] = (double)T[k]; }
   __syncthreads();
-  for (int a = tid; a < nR; a += NT) Rout[RI[a]] = Rc[a];
-  for (int b = tid; b < nL; b += NT) Lout[LJ[b]] = Lc[b];
+  for (int a = tid; a < nR; a += NT) Rout[RI[a]] = (double)Rc[a];
+  for (int b = tid; b < nL; b += NT) Lout[LJ[b]] = (double)Lc[b];
   if (tid == 0) { misc[0] = it; misc[1] = nR; misc[2] = nL; misc[3] = (int)PP.cells; }
   stamp();
 }
 
 }  // namespace
 
-size_t solve_smem_bytes(int K, int vec_in_smem) {
+size_t solve_smem_bytes(int K, int vec_in_smem, size_t fsize) {
   size_t off = ((size_t)(3 * K + 1) * sizeof(uint16_t) + 15) & ~(size_t)15;
   off += (size_t)3 * K * 4;
   off += 8 * sizeof(double);
   off += ((NW + 2) * sizeof(unsigned) + 15) & ~(size_t)15;
   off += NT * sizeof(double);
-  off += (size_t)kPieceCap * (sizeof(double) + sizeof(uint2)) + (size_t)kListCap * sizeof(unsigned);
-  if (vec_in_smem) off += (size_t)kSolveVecs * K * sizeof(double);
+  off += (size_t)kPieceCap * (fsize + sizeof(uint2)) + (size_t)kListCap * sizeof(unsigned);
+  if (vec_in_smem) off += (size_t)kSolveVecs * K * fsize;
   return off;
 }
 
-// Largest cluster (16, 8, 4, 2 or 1 CTAs) that can be resident for one image; 1 for batches.
-int solve_cluster_size(int K, int n, size_t smem) {
-  if (n != 1 || K > 1024) return 1;
+// Largest cluster (16, 8, 4, 2 or 1 CTAs) of solve_kernel<F> that can be resident for one image.
+template <typename F>
+int solve_cluster_size(size_t smem) {
   for (int C = kMaxCluster; C > 1; C >>= 1) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)C);
@@ -678,23 +685,26 @@ int solve_cluster_size(int K, int n, size_t smem) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, solve_kernel, &cfg) == cudaSuccess && nclusters > 0) return C;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, solve_kernel<F>, &cfg) == cudaSuccess && nclusters > 0) return C;
     cudaGetLastError();
   }
   return 1;
 }
 
-cudaError_t launch_solve(const SolveArgs& a, int n, cudaStream_t st) {
-  const size_t smem = solve_smem_bytes(a.K, a.vec_in_smem);
-  cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <typename F>
+cudaError_t launch_solve_t(const SolveArgs& a, int n, int cluster, cudaStream_t st) {
+  const size_t smem = solve_smem_bytes(a.K, a.vec_in_smem, sizeof(F));
+  cudaError_t e = cudaFuncSetAttribute(solve_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  e = cudaFuncSetAttribute(solve_kernel<F>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
-  static int cached_K = -1, cached_C = 1;  // per process: the cluster size for single images of this K
+  // one image: the requested cluster (vectors must be in shared memory), capped at what can be
+  // resident; batches: one CTA per image
+  static int cached_K = -1, cached_max = 1;
   int C = 1;
-  if (n == 1 && a.K <= 1024) {
-    if (cached_K != a.K) { cached_C = solve_cluster_size(a.K, 1, smem); cached_K = a.K; }
-    C = cached_C;
+  if (n == 1 && a.vec_in_smem && cluster > 1) {
+    if (cached_K != a.K) { cached_max = solve_cluster_size<F>(smem); cached_K = a.K; }
+    C = cluster < cached_max ? cluster : cached_max;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n * C));
@@ -708,7 +718,11 @@ cudaError_t launch_solve(const SolveArgs& a, int n, cudaStream_t st) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, solve_kernel, a);
+  return cudaLaunchKernelEx(&cfg, solve_kernel<F>, a);
+}
+
+cudaError_t launch_solve(const SolveArgs& a, int n, int cluster, cudaStream_t st) {
+  return a.fp32 ? launch_solve_t<float>(a, n, cluster, st) : launch_solve_t<double>(a, n, cluster, st);
 }
 
 }  // namespace hr

@@ -1,0 +1,162 @@
+"""Continuous-batching request server for HistRetinex on one GPU.
+
+Requests (host images) arrive over time.  The server keeps a FIFO queue and several CUDA
+streams, each with its own library context (a context's workspace serves one batch at a time).
+Whenever a stream is free it admits queued requests, oldest first, while the device-memory
+budget allows (input + output image + per-image workspace), copies them to the device on that
+stream, and launches one batched pipeline call for them; batches on different streams overlap
+on the device, and requests arriving while others run are admitted as soon as a stream and
+memory free up.  Results stay resident on the device.  Each request's latency runs from its
+arrival time to the completion of its batch.
+"""
+from __future__ import annotations
+
+import math
+import random
+import time
+from dataclasses import dataclass, field
+
+import paper_2510_21100_gb300 as hr
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds since the start of the run
+    image: object           # pinned host tensor (H, W, 3) uint8/uint16
+    done: float = math.nan  # completion time (seconds since the start)
+    out: object = None      # device tensor with the result (kept when keep_outputs)
+
+    @property
+    def megapixels(self) -> float:
+        return self.image.shape[0] * self.image.shape[1] / 1e6
+
+
+@dataclass
+class ServeStats:
+    completed: int
+    seconds: float
+    megapixels: float
+    latencies_ms: list = field(default_factory=list)
+    batches: int = 0
+    max_batch: int = 0
+
+    def percentile(self, q: float) -> float:
+        v = sorted(self.latencies_ms)
+        if not v:
+            return math.nan
+        k = min(len(v) - 1, max(0, int(math.ceil(q / 100.0 * len(v))) - 1))
+        return v[k]
+
+    def summary(self) -> dict:
+        return {"requests": self.completed, "seconds": self.seconds, "MP_per_s": self.megapixels / self.seconds,
+                "p50_ms": self.percentile(50), "p99_ms": self.percentile(99), "batches": self.batches,
+                "max_batch": self.max_batch}
+
+
+class Server:
+    def __init__(self, params: hr.Params | None = None, budget_bytes: int = 40 << 30, streams: int = 3,
+                 max_batch: int = 64, device: int = 0):
+        import torch
+        self.torch = torch
+        self.params = params or hr.Params()
+        self.budget = int(budget_bytes)
+        self.max_batch = max_batch
+        self.device = device
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(streams)]
+        self.ctxs = [hr.Context(self.params, device=device) for _ in range(streams)]
+        self.slot_bytes = self.ctxs[0].workspace_bytes()  # library workspace per admitted image
+
+    def _need(self, req: Request) -> int:
+        H, W = int(req.image.shape[0]), int(req.image.shape[1])
+        row = (3 * W * req.image.element_size() + 15) // 16 * 16
+        return 2 * H * row + self.slot_bytes
+
+    def run(self, requests: list[Request], keep_outputs: bool = False, poll_sleep: float = 50e-6) -> ServeStats:
+        """Serves `requests` (sorted by arrival) in real time; returns the statistics."""
+        torch = self.torch
+        pending = sorted(requests, key=lambda r: r.arrival)
+        queue: list[Request] = []
+        inflight = []  # (stream index, event, [requests], bytes)
+        free_streams = list(range(len(self.streams)))
+        used = 0
+        nxt = 0
+        batches = 0
+        max_b = 0
+        t0 = time.perf_counter()
+        done: list[Request] = []
+        while len(done) < len(pending):
+            now = time.perf_counter() - t0
+            while nxt < len(pending) and pending[nxt].arrival <= now:
+                queue.append(pending[nxt])
+                nxt += 1
+            # retire finished batches
+            still = []
+            for s, ev, reqs, nbytes in inflight:
+                if ev.query():
+                    t = time.perf_counter() - t0
+                    for r in reqs:
+                        r.done = t
+                        if not keep_outputs:
+                            r.out = None
+                    done.extend(reqs)
+                    used -= nbytes
+                    free_streams.append(s)
+                else:
+                    still.append((s, ev, reqs, nbytes))
+            inflight = still
+            # admit: one batch per free stream, oldest requests first, within the memory budget
+            while free_streams and queue:
+                batch, nbytes = [], 0
+                while queue and len(batch) < self.max_batch and used + nbytes + self._need(queue[0]) <= self.budget:
+                    r = queue.pop(0)
+                    batch.append(r)
+                    nbytes += self._need(r)
+                if not batch:
+                    if not inflight and self._need(queue[0]) > self.budget:
+                        raise ValueError(f"request {queue[0].rid} needs more device memory than the budget")
+                    break
+                s = free_streams.pop(0)
+                st = self.streams[s]
+                with torch.cuda.stream(st):
+                    ins = [hr.to_device_aligned(r.image, f"cuda:{self.device}") for r in batch]
+                    outs = [hr.aligned_empty(int(x.shape[0]), int(x.shape[1]), x.dtype, f"cuda:{self.device}")
+                            for x in ins]
+                    self.ctxs[s].enhance_batch(ins, outs, stream=st)
+                    ev = torch.cuda.Event()
+                    ev.record(st)
+                for r, o in zip(batch, outs):
+                    r.out = o
+                used += nbytes
+                inflight.append((s, ev, batch, nbytes))
+                batches += 1
+                max_b = max(max_b, len(batch))
+            if inflight and (not free_streams or not queue):
+                if nxt >= len(pending) and not queue:
+                    inflight[0][1].synchronize()  # nothing left to admit: wait for the oldest batch
+                else:
+                    time.sleep(poll_sleep)
+            elif not inflight and not queue and nxt < len(pending):
+                time.sleep(min(poll_sleep, max(0.0, pending[nxt].arrival - (time.perf_counter() - t0))))
+        seconds = max(r.done for r in done)
+        for ctx in self.ctxs:
+            ctx.check()
+        lat = [(r.done - r.arrival) * 1e3 for r in done]
+        return ServeStats(len(done), seconds, sum(r.megapixels for r in done), lat, batches, max_b)
+
+    def close(self):
+        for c in self.ctxs:
+            c.close()
+
+
+def poisson_requests(pool, rate_per_s: float, seconds: float, seed: int = 0, weights=None) -> list[Request]:
+    """Poisson arrivals over `seconds`; each request draws a pool image (by `weights` if given)."""
+    rng = random.Random(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.expovariate(rate_per_s)
+        if t >= seconds:
+            break
+        img = rng.choices(pool, weights=weights, k=1)[0]
+        out.append(Request(len(out), t, img))
+    return out
