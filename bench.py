@@ -225,6 +225,37 @@ def precision_leg(torch, hr, local, n_imgs=64, steps=2, warmup=1):
             "ms_per_batch": ms, "MP_per_s": mp / (ms / 1e3)}
 
 
+def serving_leg(torch, hr, local, big_img, seconds=5.0, rate=400.0, seed=5):
+    """Continuous batching under Poisson arrivals (mean `rate` per second) of mixed-size 8-bit
+    requests: 70% of 0.3-2 MP, 25% of 2-8 MP, 5% of 7680x4320; 40 GB device budget.  The request
+    pool holds 6 + 3 generated images and the 7680x4320 workload image."""
+    import math
+    import numpy as np
+    from paper_2510_21100_gb300 import serve, synth
+    rng = np.random.default_rng(seed)
+    pool, weights = [], []
+    for band, (lo, hi), count, share in (("small", (0.3e6, 2e6), 6, 0.70), ("medium", (2e6, 8e6), 3, 0.25)):
+        for i in range(count):
+            area = math.exp(rng.uniform(math.log(lo), math.log(hi)))
+            ar = [4 / 3, 16 / 9, 3 / 2][int(rng.integers(0, 3))]
+            w = int(round(math.sqrt(area * ar))); h = int(round(area / w))
+            pool.append(torch.from_numpy(synth.low_light_image(w, h, seed=synth.seed_for(5, len(pool)))).pin_memory())
+            weights.append(share / count)
+    pool.append(torch.from_numpy(big_img).pin_memory())
+    weights.append(0.05)
+    srv = serve.Server(hr.Params(), budget_bytes=40 << 30, streams=3, max_batch=32, device=local)
+    warm = serve.poisson_requests(pool, rate, 0.5, seed=seed + 1, weights=weights)
+    srv.run(warm)
+    reqs = serve.poisson_requests(pool, rate, seconds, seed=seed, weights=weights)
+    st = srv.run(reqs)
+    srv.close()
+    out = st.summary()
+    out.update({"workload": f"Poisson {rate:g} req/s for {seconds:g} s, 70% 0.3-2 MP / 25% 2-8 MP / 5% 7680x4320, "
+                            "uint8, K=256, 40 GB budget, 3 streams", "offered_MP_per_s":
+                    sum(r.megapixels for r in reqs) / seconds})
+    return out
+
+
 def timed_loop(ctx, dins, douts, steps, warmup, dist, torch):
     n = len(dins)
     for s in range(warmup):
@@ -369,6 +400,7 @@ def main():
         line["per_size"] = per
         line["batched"] = batched_leg(torch, hr, local)
         line["precision"] = precision_leg(torch, hr, local)
+        line["serving"] = serving_leg(torch, hr, local, imgs[0])
         rate, reps, shape = cpu_oracle_rate(imgs, seconds=10.0)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{reps} x full {shape[1]}x{shape[0]} image, single-threaded FP64 C oracle"}
