@@ -132,6 +132,24 @@ hr_status histretinex_enhance_batch(hr_ctx* ctx, int n, const void* const* d_in,
 hr_status histretinex_enhance_host(hr_ctx* ctx, const void* h_in, void* h_out, int width, int height,
                                    size_t in_pitch, size_t out_pitch, int elem_bytes, void* stream);
 
+/* Allocation-free single-image enhancement, without a context.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory at the point of the
+ * call -- code running while a framework captures a CUDA graph, real-time loops that must not
+ * block in an allocator, plug-ins whose host application owns all device memory.  It runs the
+ * same pipeline as histretinex_enhance (parameters *p as for histretinex_create, images as for
+ * histretinex_enhance) for K <= 256, with its whole workspace in one 1 MiB array that the library
+ * declares in device memory; that array stays resident on every device that loads the library
+ * until the process exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ * K > 256 returns HR_ERR_UNSUPPORTED.  The first call on a device looks up the array's device
+ * address (and the first call for a new (K, gamma) uploads the Eq. 19 table): make that first
+ * call before any stream capture.  Every call uses the same array, which keeps the previous
+ * call's contents (the call clears the histograms it accumulates); calls whose work overlaps on
+ * the GPU (other streams, other threads) race on it and must be serialised by the caller.
+ * Levels >= K are clamped but not reported.  Asynchronous on `stream`; the descriptor upload
+ * from host memory waits for the stream's earlier work. */
+hr_status histretinex_enhance_noalloc(const hr_params* p, const void* d_in, void* d_out, int width, int height,
+                                      size_t in_pitch, size_t out_pitch, int elem_bytes, void* stream);
+
 /* Intermediates of image `image` of the last enhance / enhance_batch call (index 0 for
  * enhance).  Needs HR_FLAG_DEBUG_OUT.  All outputs are HOST arrays of K entries (any may
  * be NULL): S = H_C(S), G = H_C(grad S), R = H_C(R), L = H_C(L) after Algorithm 1,

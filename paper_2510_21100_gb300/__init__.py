@@ -24,7 +24,7 @@ EXPORTS = (
     "histretinex_enhance_host", "histretinex_get_debug", "histretinex_sync_status", "histretinex_destroy",
     "histretinex_status_string", "histretinex_kernel_launches", "histretinex_stage_times",
     "histretinex_profile_solve", "histretinex_set_tuning", "histretinex_get_tuning",
-    "histretinex_workspace_bytes",
+    "histretinex_workspace_bytes", "histretinex_enhance_noalloc",
 )
 
 
@@ -91,6 +91,8 @@ def _lib():
         L.histretinex_set_tuning.restype = ctypes.c_int
         L.histretinex_get_tuning.argtypes = [vp, ctypes.POINTER(hr_tuning)]
         L.histretinex_get_tuning.restype = ctypes.c_int
+        L.histretinex_enhance_noalloc.argtypes = [ctypes.POINTER(hr_params), vp, vp, i, i, sz, sz, i, vp]
+        L.histretinex_enhance_noalloc.restype = ctypes.c_int
         L.histretinex_workspace_bytes.argtypes = [vp]
         L.histretinex_workspace_bytes.restype = ctypes.c_size_t
         for name in ("histretinex_create", "histretinex_enhance", "histretinex_enhance_batch",
@@ -170,6 +172,19 @@ def _geom(t):
     if t.stride(2) != 1 or t.stride(1) != 3:
         raise ValueError("pixels must be interleaved RGB (channel stride 1, pixel stride 3)")
     return int(t.shape[1]), int(t.shape[0]), int(t.stride(0)) * eb, eb
+
+
+def enhance_noalloc(d_in, d_out, params: "Params | None" = None, stream=None):
+    """histretinex_enhance_noalloc: one device image, no context, no device allocation (K <= 256)."""
+    W, H, pin, eb = _geom(d_in)
+    W2, H2, pout, eb2 = _geom(d_out)
+    if (W, H, eb) != (W2, H2, eb2):
+        raise ValueError("input and output images differ in shape or type")
+    cp = (params or Params()).c()
+    _check(_lib().histretinex_enhance_noalloc(ctypes.byref(cp), ctypes.c_void_p(d_in.data_ptr()),
+                                              ctypes.c_void_p(d_out.data_ptr()), W, H, pin, pout, eb,
+                                              _stream_ptr(stream)), "histretinex_enhance_noalloc")
+    return d_out
 
 
 class Context:

@@ -48,6 +48,53 @@ struct hr_ctx {
 
 namespace hr {
 
+static bool pow2(int k) { return k > 0 && (k & (k - 1)) == 0; }
+
+hr_status check_params(const hr_params* p) {
+  if (!p) return HR_ERR_INVALID_ARG;
+  if (!pow2(p->K) || p->K < 8 || p->K > 4096) return HR_ERR_INVALID_ARG;
+  if (!(p->alpha > 0.0) || !(p->beta > 0.0) || !(p->gamma > 0.0) || !(p->eps >= 0.0)) return HR_ERR_INVALID_ARG;
+  if (!std::isfinite(p->alpha) || !std::isfinite(p->beta) || !std::isfinite(p->gamma)) return HR_ERR_INVALID_ARG;
+  if (p->max_iter < 1) return HR_ERR_INVALID_ARG;
+  if (p->precision != HR_PREC_FP64 && p->precision != HR_PREC_FP32) return HR_ERR_INVALID_ARG;
+  return HR_OK;
+}
+
+// index_1(i, j) (Eq. 17-19): the level whose location k/(K-1) is nearest to the gamma-processed
+// location matrix entry (j/(K-1))^(1/gamma) * i/(K-1); the first such level on a tie.  The
+// distance is unimodal in k, so the minimum lies next to the rounded position.
+static int index1(int K, double hl, double hr) {
+  const double km1 = (double)(K - 1);
+  const double p = hl * hr;
+  long c = std::lround(p * km1);
+  long lo = c - 1 < 0 ? 0 : c - 1, hi = c + 1 > K - 1 ? K - 1 : c + 1;
+  long best = lo;
+  double bd = std::fabs(p - (double)lo / km1);
+  for (long k = lo + 1; k <= hi; ++k) {
+    const double d = std::fabs(p - (double)k / km1);
+    if (d < bd) { bd = d; best = k; }
+  }
+  return (int)best;
+}
+
+// jstart1[i][k] = first illumination bin j with index_1(i, j) >= k (index_1 grows with j).
+void build_jstart1(int K, double gamma, uint16_t* t) {
+  const double km1 = (double)(K - 1);
+  const double ig = 1.0 / gamma;
+  auto hl = [&](int j) { return std::pow((double)j / km1, ig); };
+  for (int i = 0; i < K; ++i) {
+    const double hr = (double)i / km1;
+    uint16_t* row = t + (size_t)i * (K + 1);
+    int k = 0;
+    for (int j = 0; j < K; ++j) {
+      const int c = index1(K, hl(j), hr);
+      while (k <= c) row[k++] = (uint16_t)j;
+    }
+    while (k <= K) row[k++] = (uint16_t)K;
+  }
+}
+
+
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 SlotLayout make_layout(int K) {
@@ -96,54 +143,6 @@ hr_status cuda_fail(cudaError_t e) {
     cudaError_t e_ = (x);                          \
     if (e_ != cudaSuccess) return cuda_fail(e_);   \
   } while (0)
-
-bool pow2(int k) { return k > 0 && (k & (k - 1)) == 0; }
-
-hr_status check_params(const hr_params* p) {
-  if (!p) return HR_ERR_INVALID_ARG;
-  if (!pow2(p->K) || p->K < 8 || p->K > 4096) return HR_ERR_INVALID_ARG;
-  if (!(p->alpha > 0.0) || !(p->beta > 0.0) || !(p->gamma > 0.0) || !(p->eps >= 0.0)) return HR_ERR_INVALID_ARG;
-  if (!std::isfinite(p->alpha) || !std::isfinite(p->beta) || !std::isfinite(p->gamma)) return HR_ERR_INVALID_ARG;
-  if (p->max_iter < 1) return HR_ERR_INVALID_ARG;
-  if (p->precision != HR_PREC_FP64 && p->precision != HR_PREC_FP32) return HR_ERR_INVALID_ARG;
-  return HR_OK;
-}
-
-// index_1(i, j) (Eq. 17-19): the level whose location k/(K-1) is nearest to the gamma-processed
-// location matrix entry (j/(K-1))^(1/gamma) * i/(K-1); the first such level on a tie.  The
-// distance is unimodal in k, so the minimum lies next to the rounded position.
-int index1(int K, double hl, double hr) {
-  const double km1 = (double)(K - 1);
-  const double p = hl * hr;
-  long c = std::lround(p * km1);
-  long lo = c - 1 < 0 ? 0 : c - 1, hi = c + 1 > K - 1 ? K - 1 : c + 1;
-  long best = lo;
-  double bd = std::fabs(p - (double)lo / km1);
-  for (long k = lo + 1; k <= hi; ++k) {
-    const double d = std::fabs(p - (double)k / km1);
-    if (d < bd) { bd = d; best = k; }
-  }
-  return (int)best;
-}
-
-// jstart1[i][k] = first illumination bin j with index_1(i, j) >= k (index_1 grows with j).
-void build_jstart1(int K, double gamma, std::vector<uint16_t>& t) {
-  t.assign((size_t)K * (K + 1), 0);
-  const double km1 = (double)(K - 1);
-  const double ig = 1.0 / gamma;
-  std::vector<double> hl(K);
-  for (int j = 0; j < K; ++j) hl[j] = std::pow((double)j / km1, ig);
-  for (int i = 0; i < K; ++i) {
-    const double hr = (double)i / km1;
-    uint16_t* row = t.data() + (size_t)i * (K + 1);
-    int k = 0;
-    for (int j = 0; j < K; ++j) {
-      const int c = index1(K, hl[j], hr);
-      while (k <= c) row[k++] = (uint16_t)j;
-    }
-    while (k <= K) row[k++] = (uint16_t)K;
-  }
-}
 
 void drop_graph(hr_ctx* c) {  // a captured pipeline holds workspace and descriptor pointers
   if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
@@ -342,7 +341,7 @@ void histretinex_default_params(hr_params* p) {
 hr_status histretinex_create(hr_ctx** out, const hr_params* p, int device) {
   if (!out) return HR_ERR_INVALID_ARG;
   *out = nullptr;
-  hr_status s = check_params(p);
+  hr_status s = hr::check_params(p);
   if (s != HR_OK) return s;
   int ndev = 0;
   HR_CUDA(cudaGetDeviceCount(&ndev));
@@ -354,8 +353,8 @@ hr_status histretinex_create(hr_ctx** out, const hr_params* p, int device) {
   c->p = *p;
   c->lay = hr::make_layout(p->K);
   cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
-  std::vector<uint16_t> js;
-  build_jstart1(p->K, p->gamma, js);
+  std::vector<uint16_t> js((size_t)p->K * (p->K + 1));
+  hr::build_jstart1(p->K, p->gamma, js.data());
   if (e == cudaSuccess) e = cudaMalloc(&c->d_jstart1, js.size() * sizeof(uint16_t));
   if (e == cudaSuccess) e = cudaMemcpy(c->d_jstart1, js.data(), js.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned));

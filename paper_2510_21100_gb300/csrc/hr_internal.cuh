@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/histretinex.h"
+
 namespace hr {
 
 // Device status bits, OR-ed into the context's status word by the kernels.
@@ -46,6 +48,11 @@ struct SlotLayout {
 };
 
 SlotLayout make_layout(int K);
+
+// Parameter validation of hr_params (HR_OK or HR_ERR_INVALID_ARG).
+hr_status check_params(const hr_params* p);
+// Eq. 19 class boundaries: t[i * (K + 1) + k] = first illumination bin j with index_1(i, j) >= k.
+void build_jstart1(int K, double gamma, uint16_t* t);
 
 // Number of solver vectors (double[K]) and their shared-memory footprint.
 constexpr int kSolveVecs = 8;       // Rc, Lc, L2c, RRc, Ru, Lu, q, spare
