@@ -318,8 +318,8 @@ class Context:
 
     def profile_solve(self, image: int = 0):
         """Solve-phase timestamps (ns) of the last call (needs Params(debug=True))."""
-        buf = (ctypes.c_longlong * 32)()
-        n = ctypes.c_int(32)
+        buf = (ctypes.c_longlong * 48)()
+        n = ctypes.c_int(48)
         _check(_lib().histretinex_profile_solve(self._h, image, buf, ctypes.byref(n)), "histretinex_profile_solve")
         return list(buf[: n.value])
 

@@ -108,7 +108,7 @@ SlotLayout make_layout(int K) {
   L.T = o; o += (size_t)K * 8;
   L.lut = o; o += (size_t)K * 2;
   o = align256(o);
-  L.misc = o; o += 16 + (size_t)hr::kProfSlots * 8;
+  L.misc = o; o += 16 + (size_t)kProfSlots * 8;
   o = align256(o);
   L.vec = o; o += (K > 1024) ? (size_t)kSolveVecs * K * 8 : 0;
   o = align256(o);

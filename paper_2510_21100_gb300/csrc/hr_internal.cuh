@@ -16,7 +16,7 @@ enum : unsigned { kStRange = 1u, kStTimeout = 2u, kStUnsupported = 4u };
 constexpr int kPiece = 8;
 
 // Phase timestamps (ns) the solve kernel records when asked (a measurement hook).
-constexpr int kProfSlots = 32;
+constexpr int kProfSlots = 48;
 
 // Shared-memory capacities of the solver's own cell list, pieces and piece sums; a CTA whose
 // share is larger keeps them in its global workspace instead.

@@ -431,16 +431,18 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
       }
     }
     for (int b = tid; b < nL; b += NT) { const F x = L0[b]; L2c[b] = x * x; }
+    if (it == 1) stamp();
     class_totals<F>(PP, csz, pst, R0, L0, [&](int c, F Pu) {  // (after a barrier: scal[3] is set)
       const int k = LJ[c];
       const F P = Pu * (scR * scal[3]);
       q[k] = P > 0.0 ? Sd[k] * rcpF(P) : 0.0;
     });
     __syncthreads();
+    if (it == 1) stamp();
     push_mapped(cl, q, LJ, PP.cA, PP.cB, C, rank);
     cl.sync();
     scL = scal[3];
-    if (it == 0) stamp();
+    if (it <= 1) stamp();
 
     // Eq. 13 for the own rows: lane groups of GA over the illumination bins.
     {
@@ -463,10 +465,11 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
       }
     }
     __syncthreads();
+    if (it == 1) stamp();
     push_slice(cl, R1, aA, aB, C, rank);
     push_slice(cl, RRc, aA, aB, C, rank);
     cl.sync();
-    if (it == 0) stamp();
+    if (it <= 1) stamp();
 
     // Eq. 12 for the own columns: lane groups of GB over the reflectance bins.
     if (warp == NW - 1) {  // meanwhile: 1 / denominator of Eq. 12 and the next R scale N / sum R'
@@ -492,13 +495,15 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         if (gl == 0 && b < bB) Bs[b] = acc;
       }
       __syncthreads();
+      if (it == 1) stamp();
       const F rdL = scal[1];
       for (int b = bA + tid; b < bB; b += NT) L1[b] = fma(scL * L0[b] * invN, Bs[b], alpha * Sd[LJ[b]]) * rdL;
     }
     __syncthreads();
+    if (it == 1) stamp();
     push_slice(cl, L1, bA, bB, C, rank);
     cl.sync();
-    if (it == 0) stamp();
+    if (it <= 1) stamp();
 
     const F scR1 = scal[2];
     ++it;
