@@ -165,9 +165,9 @@ hr_status ensure_desc(hr_ctx* c, int n) {
   c->d_imgs = nullptr; c->d_tile_start = nullptr; c->h_imgs = nullptr; c->h_tile_start = nullptr; c->cap_imgs = 0;
   c->last_imgs.clear();
   HR_CUDA(cudaMalloc(&c->d_imgs, sizeof(ImageDesc) * (size_t)n));
-  HR_CUDA(cudaMalloc(&c->d_tile_start, sizeof(int) * (size_t)(n + 1)));
+  HR_CUDA(cudaMalloc(&c->d_tile_start, sizeof(int) * 2 * (size_t)(n + 1)));  // tile starts, then strip starts
   HR_CUDA(cudaMallocHost(&c->h_imgs, sizeof(ImageDesc) * (size_t)n));
-  HR_CUDA(cudaMallocHost(&c->h_tile_start, sizeof(int) * (size_t)(n + 1)));
+  HR_CUDA(cudaMallocHost(&c->h_tile_start, sizeof(int) * 2 * (size_t)(n + 1)));
   c->cap_imgs = n;
   return HR_OK;
 }
@@ -197,16 +197,17 @@ hr_status fold_timing(hr_ctx* c, int i) {
 
 // The pipeline's device work on one stream: zero the histograms, histogram pass, solve, apply.
 // ev (optional): four events recorded around the three stages.
-cudaError_t enqueue_stages(hr_ctx* c, int n, int total, int elem_bytes, bool fast_in, bool fast_out, bool batched,
-                           cudaStream_t st, cudaEvent_t* ev) {
+cudaError_t enqueue_stages(hr_ctx* c, int n, int total, int units, int elem_bytes, bool fast_in, bool fast_out,
+                           bool batched, cudaStream_t st, cudaEvent_t* ev) {
   const int K = c->p.K;
   cudaError_t e;
   // zero H_C(S) and H_C(grad S) of every slot used (S and G are adjacent at the slot start)
   e = cudaMemset2DAsync(c->d_slots + c->lay.S, c->lay.bytes, 0, (size_t)2 * K * sizeof(unsigned), (size_t)n, st);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-  e = hr::launch_hist(c->d_imgs, n, c->d_tile_start, total, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay,
-                      c->d_status, c->sm_count * c->tune.hist_ctas_per_sm, st, fast_in);
+  e = hr::launch_hist(c->d_imgs, n, c->d_tile_start, total, c->d_tile_start + n + 1, units, elem_bytes, K,
+                      c->d_slots, c->lay.bytes, c->lay, c->d_status, c->sm_count, c->tune.hist_ctas_per_sm, st,
+                      fast_in);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
   hr::SolveArgs a{};
@@ -238,7 +239,7 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
   const int K = c->p.K;
   if (elem_bytes != 1 && elem_bytes != 2) return HR_ERR_INVALID_ARG;
   if (elem_bytes == 1 && K > 256) return HR_ERR_INVALID_ARG;
-  long long total = 0;
+  long long total = 0, units = 0;
   for (int i = 0; i < n; ++i) {
     const ImageDesc& d = imgs[i];
     if (!d.in || !d.out || d.W < 1 || d.H < 1) return HR_ERR_INVALID_ARG;
@@ -246,8 +247,9 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
       return HR_ERR_INVALID_ARG;
     if ((long long)d.W * d.H >= (1LL << 31)) return HR_ERR_UNSUPPORTED;
     total += hr::tiles_of(d.W, d.H);
+    units += hr::strips_of(d.W, d.H);
   }
-  if (total >= (1LL << 31)) return HR_ERR_UNSUPPORTED;
+  if (total >= (1LL << 31) || units >= (1LL << 31)) return HR_ERR_UNSUPPORTED;
   // 8-bit fast paths need every row 16-byte aligned (input for the histogram pass, both for apply)
   bool fast_in = elem_bytes == 1 && K <= 256, fast_out = fast_in;
   for (int i = 0; i < n; ++i) {
@@ -263,16 +265,19 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
   if (s != HR_OK) return s;
   if (!same_desc(c->last_imgs, imgs, n)) {
     HR_CUDA(cudaEventSynchronize(c->desc_done));  // the previous upload has left the staging buffer
-    int t = 0;
+    int t = 0, u = 0;
     for (int i = 0; i < n; ++i) {
       c->h_imgs[i] = imgs[i];
       c->h_tile_start[i] = t;
+      c->h_tile_start[n + 1 + i] = u;
       t += hr::tiles_of(imgs[i].W, imgs[i].H);
+      u += hr::strips_of(imgs[i].W, imgs[i].H);
     }
     c->h_tile_start[n] = t;
+    c->h_tile_start[2 * n + 1] = u;
     HR_CUDA(cudaMemcpyAsync(c->d_imgs, c->h_imgs, sizeof(ImageDesc) * (size_t)n, cudaMemcpyHostToDevice, st));
-    HR_CUDA(cudaMemcpyAsync(c->d_tile_start, c->h_tile_start, sizeof(int) * (size_t)(n + 1), cudaMemcpyHostToDevice,
-                            st));
+    HR_CUDA(cudaMemcpyAsync(c->d_tile_start, c->h_tile_start, sizeof(int) * 2 * (size_t)(n + 1),
+                            cudaMemcpyHostToDevice, st));
     HR_CUDA(cudaEventRecord(c->desc_done, st));
     c->last_imgs.assign(imgs, imgs + n);
   }
@@ -289,7 +294,7 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        e = enqueue_stages(c, n, (int)total, elem_bytes, fast_in, fast_out, batched, cap, nullptr);
+        e = enqueue_stages(c, n, (int)total, (int)units, elem_bytes, fast_in, fast_out, batched, cap, nullptr);
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         if (e == cudaSuccess) e = e2;
       }
@@ -316,7 +321,7 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
     ev = c->ev[i];
     c->ev_used[i] = true;
   }
-  HR_CUDA(enqueue_stages(c, n, (int)total, elem_bytes, fast_in, fast_out, batched, st, ev));
+  HR_CUDA(enqueue_stages(c, n, (int)total, (int)units, elem_bytes, fast_in, fast_out, batched, st, ev));
   c->launches += 3;
   c->last_n = n;
   return HR_OK;

@@ -74,9 +74,13 @@ struct SolveArgs {
 };
 
 // Launchers (return cudaError_t of the launch).
-cudaError_t launch_hist(const ImageDesc* d_imgs, int n, const int* d_tile_start, int total_tiles, int elem_bytes,
-                        int K, uint8_t* slots, size_t slot_bytes, SlotLayout lay, unsigned* status,
-                        int grid, cudaStream_t st, bool fast);
+// The histogram pass walks the tile list or, for one large 8-bit image with aligned rows, the
+// strip list (kStripW x kBandH units); both lists are given, with their totals.  Tile kernels
+// run sms x ctas_per_sm CTAs, the strip kernel one CTA per SM.
+cudaError_t launch_hist(const ImageDesc* d_imgs, int n, const int* d_tile_start, int total_tiles,
+                        const int* d_unit_start, int total_units, int elem_bytes, int K, uint8_t* slots,
+                        size_t slot_bytes, SlotLayout lay, unsigned* status, int sms, int ctas_per_sm,
+                        cudaStream_t st, bool fast);
 cudaError_t launch_solve(const SolveArgs& a, int n, int cluster, cudaStream_t st);
 cudaError_t launch_apply(const ImageDesc* d_imgs, int n, const int* d_tile_start, int total_tiles, int elem_bytes,
                          int K, uint8_t* slots, size_t slot_bytes, SlotLayout lay, unsigned* status, int grid,
@@ -87,5 +91,9 @@ size_t solve_smem_bytes(int K, int vec_in_smem, size_t fsize);
 constexpr int kTileW = 128;
 constexpr int kTileH = 32;
 inline int tiles_of(int W, int H) { return ((W + kTileW - 1) / kTileW) * ((H + kTileH - 1) / kTileH); }
+// Units of the 8-bit histogram pass: strips kStripW pixels wide and kBandH rows high, one warp each.
+constexpr int kStripW = 512;
+constexpr int kBandH = 8;
+inline int strips_of(int W, int H) { return ((W + kStripW - 1) / kStripW) * ((H + kBandH - 1) / kBandH); }
 
 }  // namespace hr

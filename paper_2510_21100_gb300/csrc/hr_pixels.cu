@@ -181,23 +181,384 @@ __global__ void __launch_bounds__(kThreads) apply_kernel(const ImageDesc* __rest
 }
 
 // ------------------------------------------------------------------------------------------------
-// 8-bit fast paths (rows 16-byte aligned).  The histogram pass stages each tile's rows into
-// shared memory with asynchronous 16-byte copies (double buffered: the next tile's copies run
-// while the current tile is processed), builds V four pixels per thread with byte permutes and
-// evaluates the separable Sobel operator on eight pixels per thread.  The apply pass moves 16
-// pixels (48 bytes, three 16-byte vectors) per thread each way.
+// 8-bit fast paths (rows 16-byte aligned).
+//
+// Histogram pass: one warp walks one strip of kStripW x kBandH pixels.  Lane l owns the 16
+// pixels [x0 + 16 l, x0 + 16 l + 16) of the strip's rows, so the warp reads 1536 contiguous bytes
+// per row and the warps of a CTA, dealt consecutive strips, read whole image rows together (DRAM
+// pages are read through; narrow tiles spread over many rows reached barely half the bandwidth).
+// Each lane copies its 48 bytes of the ten rows y0 - 1 .. y0 + 8 (clamped to the image: replicate
+// border) into its own shared-memory ring kRing rows ahead of use with asynchronous copies.
+// V = max(r, g, b) is kept as packed 16-bit pairs, even and odd pixels apart, so one 32-bit add
+// forms a Sobel partial sum of two pixels; the columns left and right of a lane's 16 pixels come
+// from the neighbouring lanes by shuffles, or at the strip edge from one 4-byte copy.  The squared
+// magnitude of each pair is unpacked with a sign extension and a high multiply.  Counts go to
+// per-warp shared histograms by shared-memory reductions; each CTA deals its contiguous range of
+// strips out to its warps through a shared counter.
+//
+// Apply pass: 16 pixels (48 bytes, three 16-byte vectors) per thread each way.
 // ------------------------------------------------------------------------------------------------
+#ifndef HR_HIST_WARPS
+#define HR_HIST_WARPS 16
+#endif
+constexpr int kHW = HR_HIST_WARPS;  // warps per CTA of the fast histogram pass
+constexpr int kHT = kHW * 32;
+#ifndef HR_STRIP_MIN_FACTOR
+#define HR_STRIP_MIN_FACTOR 2  // strips per warp from which one image takes the strip kernel
+#endif
+constexpr int kHBins = 256;     // per-warp histogram stride (the 8-bit pass has K <= 256)
+constexpr int kRing = 4;        // rows in flight per lane
+constexpr int kSlot = 32 * 48;  // bytes of one ring slot of a warp: 48 per lane
+
+// Shared memory of the fast histogram pass: per warp its two histograms, then per warp a ring
+// of kRing row slots (48 bytes per lane each) and of kRing neighbour words per lane.
+constexpr size_t kHistSmem = (size_t)kHW * (4 * kHBins * 4 + kRing * kSlot + kRing * 32 * 4);
+
+// One row of V around a lane's 16 pixels.
+struct VRow {
+  unsigned e[4], o[4];  // V of pixels (4w, 4w+2) and (4w+1, 4w+3) as 16-bit pairs, w = 0..3
+  unsigned l, r;        // high half of l: V of the pixel left of the 16; low half of r: the one right
+};
+
+// Per-lane geometry of the current tile and the lane's ring slots.
+struct LaneTile {
+  const uint8_t* in;
+  long long pitch;
+  int W, H;
+  int x0, xc, cnt;      // tile origin column, first column of the lane, W - xc
+  int lx;
+  unsigned char* ring;  // the lane's 48 bytes in slot 0 (slot s at + s * kSlot)
+  unsigned* nbr;        // the lane's neighbour word in slot 0 (slot s at + s * 32)
+};
+
+__device__ __forceinline__ const uint8_t* row_ptr(const LaneTile& g, int y) {
+  return g.in + (long long)clampi(y, 0, g.H - 1) * g.pitch;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+// 16-byte copy of which only the first `nb` (0..16) bytes are read; the rest is zero-filled.
+__device__ __forceinline__ void cp_async16z(void* smem_dst, const void* gsrc, int nb) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "r"(nb) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Starts the copies of row y into ring slot `slot` (one commit group per call; empty when
+// `live` is false): the lane's 48 bytes (a lane holding the image's last 1..15 pixels reads only
+// the row's own bytes and gets zeros after them), and the 4-byte neighbour word of lanes 0 and
+// 31.  Only the lane itself reads what it copied, so its own wait_group orders copies and reads.
+__device__ __forceinline__ void issue_row(const LaneTile& g, int slot, int y, bool live) {
+  if (live) {
+    const uint8_t* row = row_ptr(g, y);
+    unsigned char* dst = g.ring + slot * kSlot;
+    const uint8_t* src = row + 3 * g.xc;
+    if (g.cnt >= 16) {
+      cp_async16(dst, src);
+      cp_async16(dst + 16, src + 16);
+      cp_async16(dst + 32, src + 32);
+    } else if (g.cnt > 0) {
+      const int nb = 3 * g.cnt;  // 3 .. 45 bytes of the row remain
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int b = min(max(nb - 16 * i, 0), 16);
+        cp_async16z(dst + 16 * i, b > 0 ? (const void*)(src + 16 * i) : (const void*)row, b);
+      }
+    }
+    if (g.lx == 0 && g.x0 > 0) cp_async4(g.nbr + slot * 32, row + 3 * g.x0 - 4);
+    else if (g.lx == 31 && g.x0 + kStripW + 2 <= g.W) cp_async4(g.nbr + slot * 32, row + 3 * (g.x0 + kStripW));
+  }
+  cp_async_commit();
+}
+
+// V of two pixels as 16-bit pairs from the 12 bytes of four pixels: a = R0 G0 B0 R1,
+// b = G1 B1 R2 G2, c = B2 R3 G3 B3.  Every operand of one 3-way max carries the same filler
+// byte above each channel byte, so the halfword maximum is the channel maximum.
+__device__ __forceinline__ void vpairs(unsigned a, unsigned b, unsigned c, unsigned& e, unsigned& o) {
+  e = __vimax3_u16x2(__byte_perm(a, b, 0x3630), __byte_perm(a, b, 0x3731), __byte_perm(a, c, 0x3432)) & 0x00ff00ffu;
+  o = __vimax3_u16x2(__byte_perm(a, c, 0x4543), __byte_perm(b, c, 0x4640), __byte_perm(b, c, 0x4741)) & 0x00ff00ffu;
+}
+
+__device__ __forceinline__ unsigned max3b(unsigned w, int s0) {  // max of bytes s0, s0+1, s0+2 of w
+  return max(max((w >> (8 * s0)) & 0xffu, (w >> (8 * s0 + 8)) & 0xffu), (w >> (8 * s0 + 16)) & 0xffu);
+}
+
+// V row of one lane from ring slot `slot` (row y); all lanes of the warp call it together.
+// Positions right of the image's last pixel hold zeros, except the first one, which holds the
+// replica of the last pixel (replicate border).
+template <bool kEdge, bool kClamp>
+__device__ __forceinline__ VRow build_row(const LaneTile& g, int slot, int y, unsigned kk, bool& bad) {
+  VRow v;
+  const unsigned char* qb = g.ring + slot * kSlot;
+  {
+    const uint4* q = reinterpret_cast<const uint4*>(qb);
+    const uint4 a = q[0], b = q[1], c = q[2];
+    vpairs(a.x, a.y, a.z, v.e[0], v.o[0]);
+    vpairs(a.w, b.x, b.y, v.e[1], v.o[1]);
+    vpairs(b.z, b.w, c.x, v.e[2], v.o[2]);
+    vpairs(c.y, c.z, c.w, v.e[3], v.o[3]);
+  }
+  if (kEdge && g.cnt <= 0) {  // lane right of the image: nothing was copied, nothing is counted
+#pragma unroll
+    for (int w = 0; w < 4; ++w) v.e[w] = v.o[w] = 0u;
+  }
+  if (kClamp) {  // K < 256: levels above K - 1 are a range error, clamped so counting stays in bounds
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const unsigned ce = __vimin3_u16x2(v.e[w], kk, kk), co = __vimin3_u16x2(v.o[w], kk, kk);
+      bad |= (ce != v.e[w]) | (co != v.o[w]);
+      v.e[w] = ce;
+      v.o[w] = co;
+    }
+  }
+  // neighbour columns: from the adjacent lanes of the lane row, else from the neighbour word
+  v.l = __shfl_up_sync(0xffffffffu, v.o[3], 1);
+  v.r = __shfl_down_sync(0xffffffffu, v.e[0], 1);
+  if (g.lx == 0) {
+    unsigned lv = v.e[0] & 0xffffu;  // x0 == 0: replicate pixel 0
+    if (g.x0 > 0) lv = max3b(g.nbr[slot * 32], 1);
+    if (kClamp) { bad |= lv > (kk & 0xffffu); lv = min(lv, kk & 0xffffu); }
+    v.l = lv << 16;
+  }
+  if (g.xc + 16 >= g.W) {  // the lane holds the image's last pixel: replicate it to its right
+    if (!kEdge || g.cnt >= 16) {
+      v.r = v.o[3] >> 16;
+    } else if (g.cnt > 0) {
+      const unsigned char* lp = qb + 3 * (g.cnt - 1);
+      unsigned vlast = max(max((unsigned)lp[0], (unsigned)lp[1]), (unsigned)lp[2]);
+      if (kClamp) vlast = min(vlast, kk & 0xffffu);
+      v.r = vlast;
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {  // pixel cnt (zero-filled) becomes the replica
+        if (4 * w == g.cnt) v.e[w] = (v.e[w] & 0xffff0000u) | vlast;
+        if (4 * w + 2 == g.cnt) v.e[w] = (v.e[w] & 0x0000ffffu) | (vlast << 16);
+        if (4 * w + 1 == g.cnt) v.o[w] = (v.o[w] & 0xffff0000u) | vlast;
+        if (4 * w + 3 == g.cnt) v.o[w] = (v.o[w] & 0x0000ffffu) | (vlast << 16);
+      }
+    }
+  } else if (g.lx == 31) {
+    unsigned rv;
+    if (g.x0 + kStripW + 2 <= g.W) {
+      rv = max3b(g.nbr[slot * 32], 0);
+    } else {  // the right neighbour is the image's last pixel
+      const uint8_t* p = row_ptr(g, y) + 3 * (g.x0 + kStripW);
+      rv = max(max((unsigned)p[0], (unsigned)p[1]), (unsigned)p[2]);
+    }
+    if (kClamp) { bad |= rv > (kk & 0xffffu); rv = min(rv, kk & 0xffffu); }
+    v.r = rv;
+  }
+  return v;
+}
+
+__device__ __forceinline__ void red_shared(unsigned addr) {
+  asm volatile("red.shared.add.u32 [%0], 1;\n" ::"r"(addr) : "memory");
+}
+
+// Counts one pixel: V level v into H_C(S); its gradient level, the nearest integer to sqrt(m2)
+// clipped to K - 1, into H_C(grad S).  Clipping m2 at K^2 - K first gives the same level, keeps
+// m2 below 2^23 so float(m2) is the magic-number conversion, and sqrt.approx is within 2^-19
+// relative of sqrt(m2) there, well inside the distance 1/(4 sqrt(m2) + 2) from sqrt(m2) to the
+// nearest half integer, so the round-to-nearest add of 2^23 yields the exact level
+// (0x4B000000 + level in the float's bits; hg_adj absorbs the 0x4B000000).
+__device__ __forceinline__ void count_px(int m2, unsigned v, int mclip, unsigned hs_sh, unsigned hg_adj, bool on) {
+  const int m2c = min(m2, mclip);
+  const float f = __fsub_rn(__int_as_float(0x4B000000 | m2c), 8388608.0f);
+  float s;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(s) : "f"(f));
+  const unsigned gb = __float_as_uint(__fadd_rn(s, 8388608.0f));
+  if (on) {
+    red_shared(hg_adj + (gb << 2));
+    red_shared(hs_sh + (v << 2));
+  }
+}
+
+// Two pixels from packed Sobel components: each 32-bit word is HI * 65536 + LO with LO, HI the
+// signed components of the low and high pixel (exact: the packed adds never carry out of a
+// half by more than the borrow this form absorbs).
+__device__ __forceinline__ void count_pair(int gx, int gy, unsigned vpair, int p0, int lim, int mclip,
+                                           unsigned hs_sh, unsigned hg_adj) {
+  const int ax = (int)(short)gx, ay = (int)(short)gy;
+  const int m2a = ax * ax + ay * ay;
+  const int dx = gx - ax, dy = gy - ay;
+  const int m2b = __mulhi(dx, dx) + __mulhi(dy, dy);
+  count_px(m2a, vpair & 0xffffu, mclip, hs_sh, hg_adj, p0 < lim);
+  count_px(m2b, vpair >> 16, mclip, hs_sh, hg_adj, p0 + 2 < lim);
+}
+
+// Separable Sobel (gx: right minus left column of [1 2 1]^T-weighted sums; gy: bottom minus top
+// row of [1 2 1]-weighted sums) and counting for the output row M between rows T and B.
+__device__ __forceinline__ void count_row(const VRow& T, const VRow& M, const VRow& B, int lim, int mclip,
+                                          unsigned hs_sh, unsigned hg_adj) {
+  // column sums cs = T + 2 M + B and differences dd = B - T + 256 per half (in [1, 511]), formed
+  // word by word as the window over the four pairs moves right
+  auto cs = [](unsigned t, unsigned m, unsigned b) { return t + b + 2u * m; };
+  auto dd = [](unsigned t, unsigned b) { return b - t + 0x01000100u; };
+  unsigned csOp = cs(T.l, M.l, B.l), ddOp = dd(T.l, B.l);  // odd pair left of pair 0 (high half: x - 1)
+  unsigned csEc = cs(T.e[0], M.e[0], B.e[0]), ddEc = dd(T.e[0], B.e[0]);
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    const unsigned csOc = cs(T.o[w], M.o[w], B.o[w]), ddOc = dd(T.o[w], B.o[w]);
+    const unsigned csEn = w < 3 ? cs(T.e[w + 1], M.e[w + 1], B.e[w + 1]) : cs(T.r, M.r, B.r);
+    const unsigned ddEn = w < 3 ? dd(T.e[w + 1], B.e[w + 1]) : dd(T.r, B.r);
+    // odd pixels left of the even pair (4w-1, 4w+1); even pixels right of the odd pair (4w+2, 4w+4)
+    const unsigned csOL = __byte_perm(csOp, csOc, 0x5432), ddOL = __byte_perm(ddOp, ddOc, 0x5432);
+    const unsigned csER = __byte_perm(csEc, csEn, 0x5432), ddER = __byte_perm(ddEc, ddEn, 0x5432);
+    const int gxE = (int)(csOc - csOL);
+    const int gyE = (int)(ddOL + 2u * ddEc + ddOc - 0x04000400u);
+    const int gxO = (int)(csER - csEc);
+    const int gyO = (int)(ddEc + 2u * ddOc + ddER - 0x04000400u);
+    count_pair(gxE, gyE, M.e[w], 4 * w, lim, mclip, hs_sh, hg_adj);
+    count_pair(gxO, gyO, M.o[w], 4 * w + 1, lim, mclip, hs_sh, hg_adj);
+    csOp = csOc; ddOp = ddOc; csEc = csEn; ddEc = ddEn;
+  }
+}
+
+// One tile for one lane; returns whether a level above K - 1 was seen.  Rows yb .. yb + 9 go
+// through the lane's ring, kRing rows ahead of use.
+template <bool kEdge, bool kClamp>
+__device__ __forceinline__ bool hist_tile(const LaneTile& g, int yb, int mclip, unsigned kk, unsigned hs_sh,
+                                          unsigned hg_adj) {
+  constexpr int kRows = kBandH + 2;
+  bool bad = false;
+#pragma unroll
+  for (int r = 0; r < kRing; ++r) issue_row(g, r, yb + r, true);
+  cp_async_wait<kRing - 1>();
+  VRow v0 = build_row<kEdge, kClamp>(g, 0, yb, kk, bad);
+  issue_row(g, 0, yb + kRing, kRing < kRows);
+  cp_async_wait<kRing - 1>();
+  VRow v1 = build_row<kEdge, kClamp>(g, 1, yb + 1, kk, bad);
+  issue_row(g, 1, yb + kRing + 1, kRing + 1 < kRows);
+  const int full = kEdge ? min(g.cnt, 16) : 16;
+#pragma unroll
+  for (int j = 0; j < kBandH; ++j) {
+    cp_async_wait<kRing - 1>();
+    const VRow v2 = build_row<kEdge, kClamp>(g, (j + 2) % kRing, yb + j + 2, kk, bad);
+    issue_row(g, (j + 2) % kRing, yb + j + 2 + kRing, j + 2 + kRing < kRows);
+    const int lim = kEdge ? (yb + j + 1 < g.H ? full : 0) : 16;
+    count_row(v0, v1, v2, lim, mclip, hs_sh, hg_adj);
+    v0 = v1;
+    v1 = v2;
+  }
+  return bad;
+}
+
+// Tiles that cross the image's right or bottom edge, kept out of line so the interior path has
+// the register file to itself.
+template <bool kClamp>
+__device__ __noinline__ bool hist_tile_edge(const LaneTile g, int yb, int mclip, unsigned kk, unsigned hs_sh,
+                                            unsigned hg_adj) {
+  return hist_tile<true, kClamp>(g, yb, mclip, kk, hs_sh, hg_adj);
+}
+
+template <bool kClamp>
+__global__ void __launch_bounds__(kHT, 1) hist_u8r_kernel(const ImageDesc* __restrict__ imgs, int n,
+                                                         const int* __restrict__ unit_start, int total, int K,
+                                                         uint8_t* slots, size_t slot_bytes, SlotLayout lay,
+                                                         unsigned* status) {
+  extern __shared__ __align__(16) unsigned char hsmem[];
+  // per warp two copies (even and odd lanes, which see the most alike levels) of H_C(S), H_C(grad S)
+  auto hist = reinterpret_cast<unsigned (*)[2][2][kHBins]>(hsmem);
+  unsigned char* ring = hsmem + (size_t)kHW * 4 * kHBins * 4;
+  unsigned* nbr = reinterpret_cast<unsigned*>(ring + (size_t)kHW * kRing * kSlot);
+  __shared__ int next_tile;
+  __shared__ int warp_img[kHW];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned* hw = &hist[warp][0][0][0];
+  for (int k = lane; k < 4 * kHBins; k += 32) hw[k] = 0u;
+  const int chunk = (total + gridDim.x - 1) / gridDim.x;
+  const int t0 = blockIdx.x * chunk, t1 = min(total, t0 + chunk);
+  if (tid == 0) next_tile = t0;
+  __syncthreads();
+
+  const unsigned hs_sh = (unsigned)__cvta_generic_to_shared(hist[warp][lane & 1][0]);
+  const unsigned hg_adj = (unsigned)__cvta_generic_to_shared(hist[warp][lane & 1][1]) - 0x2C000000u;  // - (0x4B000000 << 2)
+  const int mclip = K * K - K;
+  const unsigned kk = 0x00010001u * (unsigned)(K - 1);
+  LaneTile g;
+  g.lx = lane;
+  g.ring = ring + (size_t)warp * kRing * kSlot + 48 * lane;
+  g.nbr = nbr + warp * kRing * 32 + lane;
+  int cur = -1;
+  bool bad = false;
+  auto flush_warp = [&](int im_idx) {
+    __syncwarp();
+    unsigned* S = reinterpret_cast<unsigned*>(slots + (size_t)im_idx * slot_bytes + lay.S);
+    unsigned* G = reinterpret_cast<unsigned*>(slots + (size_t)im_idx * slot_bytes + lay.G);
+    for (int k = lane; k < K; k += 32) {
+      const unsigned sv = hist[warp][0][0][k] + hist[warp][1][0][k], gv = hist[warp][0][1][k] + hist[warp][1][1][k];
+      hist[warp][0][0][k] = hist[warp][1][0][k] = hist[warp][0][1][k] = hist[warp][1][1][k] = 0u;
+      if (sv) atomicAdd(S + k, sv);
+      if (gv) atomicAdd(G + k, gv);
+    }
+    __syncwarp();
+  };
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(&next_tile, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= t1) break;
+    const int img = image_of_tile(unit_start, n, t);
+    if (img != cur) {
+      if (cur >= 0) flush_warp(cur);
+      cur = img;
+    }
+    const ImageDesc& im = imgs[img];
+    g.in = im.in;
+    g.pitch = im.in_pitch;
+    g.W = im.W;
+    g.H = im.H;
+    const int lt = t - __ldg(unit_start + img);
+    const int strips_x = (g.W + kStripW - 1) / kStripW;
+    g.x0 = (lt % strips_x) * kStripW;
+    const int y0 = (lt / strips_x) * kBandH;
+    g.xc = g.x0 + 16 * g.lx;
+    g.cnt = g.W - g.xc;
+    const int yb = y0 - 1;
+    const bool edge = g.x0 + kStripW > g.W || y0 + kBandH > g.H;
+    if (edge) bad |= hist_tile_edge<kClamp>(g, yb, mclip, kk, hs_sh, hg_adj);
+    else bad |= hist_tile<false, kClamp>(g, yb, mclip, kk, hs_sh, hg_adj);
+  }
+  // the warps' last images: sum the warps that share an image, one global add per level
+  if (lane == 0) warp_img[warp] = cur;
+  __syncthreads();
+  {
+    for (int idx = tid; idx < 2 * kHBins; idx += kHT) {
+      const int which = idx / kHBins, k = idx % kHBins;
+      if (k >= K) continue;
+      for (int w = 0; w < kHW; ++w) {
+        const int im_idx = warp_img[w];
+        bool first = im_idx >= 0;
+        for (int u = 0; u < w && first; ++u) first = warp_img[u] != im_idx;
+        if (!first) continue;
+        unsigned s = 0;
+        for (int u = w; u < kHW; ++u)
+          if (warp_img[u] == im_idx) s += hist[u][0][which][k] + hist[u][1][which][k];
+        unsigned* dst = reinterpret_cast<unsigned*>(slots + (size_t)im_idx * slot_bytes + (which ? lay.G : lay.S));
+        if (s) atomicAdd(dst + k, s);
+      }
+    }
+  }
+  if (bad) atomicOr(status, kStRange);
+}
+
+// Staged-tile histogram pass for small images and batches: a CTA per 128 x 32 tile, its rows
+// staged into shared memory by asynchronous 16-byte copies (double buffered: the next tile's
+// copies run while the current tile is processed); V is built four pixels per thread with byte
+// permutes and the separable Sobel operator evaluated on eight pixels per thread.  With eight
+// warps on each tile it has the parallelism small launches need; the strip kernel above reads
+// large images faster.
 constexpr int kRawRow = 416;              // staged bytes per tile row: [3 x0 - 16, 3 x0 + 400)
 constexpr int kRawChunks = kRawRow / 16;
 constexpr int kVTS = 136;                 // V tile row stride; column c holds x = x0 - 4 + c
 constexpr int kVGroups = kVTS / 4;        // 4-pixel groups per V tile row
-
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, int src_bytes) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // Issues the copies of tile (x0, y0) of `im`: rows y0-1 .. y0+32 (clamped), bytes
 // [3 x0 - 16, 3 x0 + 400) of each row; bytes outside the row are zero-filled and never read.
@@ -211,7 +572,7 @@ __device__ __forceinline__ void stage_tile(const ImageDesc& im, int x0, int y0, 
     const long long b0 = start + 16LL * ch;
     int nb = 0;
     if (b0 >= 0 && b0 < rowbytes) nb = (int)(rowbytes - b0 < 16 ? rowbytes - b0 : 16);
-    cp_async16(raw + r * kRawRow + ch * 16, nb > 0 ? (const void*)(row + b0) : (const void*)row, nb);
+    cp_async16z(raw + r * kRawRow + ch * 16, nb > 0 ? (const void*)(row + b0) : (const void*)row, nb);
   }
   cp_async_commit();
 }
@@ -291,7 +652,7 @@ __global__ void __launch_bounds__(kThreads) hist_u8v_kernel(const ImageDesc* __r
     } else {
       cp_async_commit();
     }
-    cp_async_wait1();
+    cp_async_wait<1>();
     __syncthreads();
     if (img != cur) {
       if (cur >= 0) flush(cur);
@@ -439,11 +800,28 @@ __global__ void __launch_bounds__(kThreads) apply_u8v_kernel(const ImageDesc* __
 
 }  // namespace
 
-cudaError_t launch_hist(const ImageDesc* d_imgs, int n, const int* d_tile_start, int total_tiles, int elem_bytes,
-                        int K, uint8_t* slots, size_t slot_bytes, SlotLayout lay, unsigned* status, int grid,
+cudaError_t launch_hist(const ImageDesc* d_imgs, int n, const int* d_tile_start, int total_tiles,
+                        const int* d_unit_start, int total_units, int elem_bytes, int K, uint8_t* slots,
+                        size_t slot_bytes, SlotLayout lay, unsigned* status, int sms, int ctas_per_sm,
                         cudaStream_t st, bool fast) {
   const int copies = K <= 256 ? kWarps : 1;
   const size_t smem = (size_t)2 * copies * K * sizeof(unsigned) + (size_t)kVH * kVW * sizeof(unsigned short);
+  // strips for one large image (at least HR_STRIP_MIN_FACTOR per warp of a full grid), staged
+  // tiles otherwise
+  if (elem_bytes == 1 && fast && K <= kHBins && n == 1 && total_units >= HR_STRIP_MIN_FACTOR * sms * kHW) {
+    const int grid = sms;
+    if (K < kHBins) {
+      cudaFuncSetAttribute(hist_u8r_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem);
+      hist_u8r_kernel<true><<<grid, kHT, kHistSmem, st>>>(d_imgs, n, d_unit_start, total_units, K, slots, slot_bytes,
+                                                          lay, status);
+    } else {
+      cudaFuncSetAttribute(hist_u8r_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem);
+      hist_u8r_kernel<false><<<grid, kHT, kHistSmem, st>>>(d_imgs, n, d_unit_start, total_units, K, slots,
+                                                           slot_bytes, lay, status);
+    }
+    return cudaGetLastError();
+  }
+  int grid = sms * ctas_per_sm;
   if (grid > total_tiles) grid = total_tiles;
   if (grid < 1) grid = 1;
   if (elem_bytes == 1 && fast) {

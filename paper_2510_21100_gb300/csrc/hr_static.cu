@@ -85,8 +85,8 @@ extern "C" hr_status histretinex_enhance_noalloc(const hr_params* p, const void*
   }
   const hr::ImageDesc desc{static_cast<const uint8_t*>(d_in), static_cast<uint8_t*>(d_out), width, height,
                            (long long)in_pitch, (long long)out_pitch};
-  const int tiles = hr::tiles_of(width, height);
-  const int tile_start[2] = {0, tiles};
+  const int tiles = hr::tiles_of(width, height), units = hr::strips_of(width, height);
+  const int tile_start[4] = {0, tiles, 0, units};  // tile list, then strip list
   cudaError_t e = cudaMemcpyAsync(base + off_desc, &desc, sizeof(desc), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(base + off_tiles, tile_start, sizeof(tile_start), cudaMemcpyHostToDevice, st);
   // what must start at zero: the two histograms and the status word
@@ -101,7 +101,8 @@ extern "C" hr_status histretinex_enhance_noalloc(const hr_params* p, const void*
   auto* d_status = reinterpret_cast<unsigned*>(base + off_status);
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return HR_ERR_CUDA;
-  e = hr::launch_hist(d_desc, 1, d_tiles, tiles, elem_bytes, K, base, lay.bytes, lay, d_status, sms * 8, st, fast_in);
+  e = hr::launch_hist(d_desc, 1, d_tiles, tiles, d_tiles + 2, units, elem_bytes, K, base, lay.bytes, lay, d_status,
+                      sms, 8, st, fast_in);
   if (e != cudaSuccess) return HR_ERR_CUDA;
   hr::SolveArgs a{};
   a.K = K;

@@ -189,6 +189,40 @@ def test_full_size_single_images(hr, W, H):
     compare_to_oracle(img, out, dbg, po)
 
 
+def _strip_pad(W):
+    """Row padding (elements) that makes 3 W + pad a multiple of 16: 16-byte aligned rows."""
+    return (-3 * W) % 16
+
+
+def test_large_ragged_image(hr):
+    """A single image large enough for the strip histogram kernel (one warp per 512 x 8 strip),
+    with a partial last strip (7001 = 13 * 512 + 345: a lane holding 9 pixels) and a partial last
+    band (4001 = 500 * 8 + 1)."""
+    ctx, po = ctx_for(hr)
+    img = synth.low_light_image(7001, 4001, seed=synth.seed_for(1, 7))
+    out, dbg = run_gpu(ctx, img, pad_elems=_strip_pad(7001))
+    compare_to_oracle(img, out, dbg, po)
+
+
+def test_large_image_below_256_levels(hr):
+    """The strip kernel's clamping path (K < 256) on in-range data."""
+    ctx, po = ctx_for(hr, K=128)
+    img = np.minimum(synth.low_light_image(6145, 3203, seed=synth.seed_for(1, 8)), 127).astype(np.uint8)
+    out, dbg = run_gpu(ctx, img, pad_elems=_strip_pad(6145))
+    compare_to_oracle(img, out, dbg, po)
+
+
+def test_large_image_level_out_of_range_is_reported(hr):
+    import paper_2510_21100_gb300 as hrm
+    ctx, _ = ctx_for(hr, K=64)
+    img = synth.low_light_image(7680, 4320, seed=synth.seed_for(1, 9))
+    assert img.max() >= 64
+    import torch
+    d = torch.from_numpy(img).cuda()
+    ctx.enhance(d, torch.empty_like(d))
+    assert ctx.sync_status() == hrm.ERR_RANGE
+
+
 def test_repeated_calls_are_deterministic(hr):
     ctx, _ = ctx_for(hr)
     img = synth.low_light_image(640, 480, seed=8)
