@@ -155,10 +155,11 @@ def run_reference(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def batched_leg(torch, hr, local, n_imgs=512, steps=10, warmup=3, seed=3):
+def batched_leg(torch, hr, local, precision, n_imgs=512, steps=10, warmup=3, seed=3):
     """The batched form: n mixed-size 8-bit images (areas log-uniform in 320x240 .. 1920x1080, aspect
     4:3/16:9/3:2) per graph-replayed batch call.  Images are crops of 16 generated 1920x1248 images
-    (the largest 4:3 image of that area is 1663x1247)."""
+    (the largest 4:3 image of that area is 1663x1247).  precision: the solve's arithmetic (FP64, or
+    double-float, which the GPU tests hold to the same tolerance)."""
     import numpy as np
     from paper_2510_21100_gb300 import autotune, synth
     sizes = synth.mixed_batch_sizes(n_imgs, seed)
@@ -176,7 +177,7 @@ def batched_leg(torch, hr, local, n_imgs=512, steps=10, warmup=3, seed=3):
         t.copy_(b[y:y + h, x:x + w])
         ins.append(t)
     outs = [hr.aligned_empty(int(t.shape[0]), int(t.shape[1]), device=f"cuda:{local}") for t in ins]
-    ctx = hr.Context(hr.Params(), device=local)
+    ctx = hr.Context(hr.Params(precision=precision), device=local)
     tune, _ = autotune.autotune(ctx, ins, outs, reps=2, cache_path=None)
     mp = sum(w * h for w, h in sizes) / 1e6
     for _ in range(warmup):
@@ -192,7 +193,9 @@ def batched_leg(torch, hr, local, n_imgs=512, steps=10, warmup=3, seed=3):
     ctx.check()
     ms = e0.elapsed_time(e1) / steps
     byts = 3 * 3 * mp * 1e6  # read for the histograms, read + write for the apply
-    return {"workload": f"{n_imgs} mixed uint8 images, {mp:.1f} MP per batch call, K=256, T=10", "images": n_imgs,
+    arith = {hr.PREC_FP64: "FP64", hr.PREC_DF64: "double-float"}[precision]
+    return {"workload": f"{n_imgs} mixed uint8 images, {mp:.1f} MP per batch call, K=256, T=10, {arith} solve",
+            "images": n_imgs,
             "MP": mp, "ms_per_batch": ms, "MP_per_s": mp / (ms / 1e3), "tuning": tune,
             "gpu_launches_per_batch": (ctx.kernel_launches() - l0) / steps, "pipeline_GBps": byts / (ms / 1e3) / 1e9}
 
@@ -398,7 +401,8 @@ def main():
                                  "roofline_frac": rl / ms2}
             c2.close()
         line["per_size"] = per
-        line["batched"] = batched_leg(torch, hr, local)
+        line["batched"] = batched_leg(torch, hr, local, hr.PREC_DF64)
+        line["batched_fp64"] = batched_leg(torch, hr, local, hr.PREC_FP64)
         line["precision"] = precision_leg(torch, hr, local)
         line["serving"] = serving_leg(torch, hr, local, imgs[0])
         rate, reps, shape = cpu_oracle_rate(imgs, seconds=10.0)

@@ -57,7 +57,10 @@ typedef enum {
 
 typedef enum {
   HR_PREC_FP64 = 0,        /* the plain form: the K-dimensional solve in FP64 */
-  HR_PREC_FP32 = 1         /* reduced precision: solve sums in FP32 (histograms, CDFs exact; LUT compare in FP64) */
+  HR_PREC_FP32 = 1,        /* reduced precision: solve sums in FP32 (histograms, CDFs exact; LUT compare in FP64) */
+  HR_PREC_DF64 = 4         /* the solve in double-float pairs of FP32 numbers (about 2^-47 relative per
+                              operation, within the plain form's tolerance of the FP64 result), for
+                              throughput where the FP64 rate is low; LUT compare in FP64 */
 } hr_precision;
 
 enum {

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libhistretinex.so")
 
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_RANGE, ERR_TIMEOUT = range(7)
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_DF64 = 0, 1, 4
 FLAG_FIXED_ITERS, FLAG_DEBUG_OUT, FLAG_STAGE_TIMING = 1, 2, 4
 
 # Every symbol include/histretinex.h declares.

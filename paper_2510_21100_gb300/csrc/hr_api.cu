@@ -56,7 +56,8 @@ hr_status check_params(const hr_params* p) {
   if (!(p->alpha > 0.0) || !(p->beta > 0.0) || !(p->gamma > 0.0) || !(p->eps >= 0.0)) return HR_ERR_INVALID_ARG;
   if (!std::isfinite(p->alpha) || !std::isfinite(p->beta) || !std::isfinite(p->gamma)) return HR_ERR_INVALID_ARG;
   if (p->max_iter < 1) return HR_ERR_INVALID_ARG;
-  if (p->precision != HR_PREC_FP64 && p->precision != HR_PREC_FP32) return HR_ERR_INVALID_ARG;
+  if (p->precision != HR_PREC_FP64 && p->precision != HR_PREC_FP32 && p->precision != HR_PREC_DF64)
+    return HR_ERR_INVALID_ARG;
   return HR_OK;
 }
 
@@ -224,7 +225,7 @@ cudaError_t enqueue_stages(hr_ctx* c, int n, int total, int units, int elem_byte
   a.status = c->d_status;
   a.vec_in_smem = K <= 1024 ? 1 : 0;
   a.profile = (c->p.flags & HR_FLAG_DEBUG_OUT) ? 1 : 0;
-  a.fp32 = c->p.precision == HR_PREC_FP32 ? 1 : 0;
+  a.arith = c->p.precision == HR_PREC_FP32 ? hr::kArithF32 : (c->p.precision == HR_PREC_DF64 ? hr::kArithDF64 : hr::kArithF64);
   e = hr::launch_solve(a, n, batched ? 1 : c->tune.solve_cluster, st);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;

@@ -58,6 +58,9 @@ void build_jstart1(int K, double gamma, uint16_t* t);
 constexpr int kSolveVecs = 8;       // Rc, Lc, L2c, RRc, Ru, Lu, q, spare
 constexpr int kSolveThreads = 512;
 
+// Arithmetic of the solve's sums.
+enum : int { kArithF64 = 0, kArithF32 = 1, kArithDF64 = 2 };
+
 struct SolveArgs {
   int K;
   double alpha, beta, eps;
@@ -70,7 +73,7 @@ struct SolveArgs {
   unsigned* status;
   int vec_in_smem;           // 1: solver vectors in dynamic shared memory
   int profile;               // 1: record phase timestamps into the slot's misc area
-  int fp32;                  // 1: solve sums in FP32 (reduced-precision form), else FP64
+  int arith;                 // kArithF64 (plain form), kArithF32 (reduced precision), kArithDF64
 };
 
 // Launchers (return cudaError_t of the launch).

@@ -45,9 +45,81 @@ __device__ __forceinline__ double rcp64(double d) {
   return fma(r, e, r);
 }
 
-// 1/d in the solver's arithmetic: FP64 (plain form) or FP32 (reduced-precision form).
+// a b + c and 1/d in the solver's arithmetic: FP64 (plain form), FP32 (reduced-precision form) or
+// double-float.
+__device__ __forceinline__ double fmaF(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmaF(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double rcpF(double d) { return rcp64(d); }
 __device__ __forceinline__ float rcpF(float d) { return __frcp_rn(d); }
+
+// Double-float arithmetic: a value is hi + lo, two FP32 numbers with |lo| <= ulp(hi) / 2,
+// carried through error-free transformations (Dekker and Knuth: the exact rounding error of a
+// sum from Knuth's two-sum, that of a product from one fused multiply-add).  Every operation
+// keeps about 2^-47 relative accuracy on FP32's exponent range (all values of the solve lie
+// between 1e-30 and 1e20 for images below 2^31 pixels).  GB300 runs FP32 at 64 times its FP64
+// rate, so a dozen FP32 operations per step still outrun one FP64 operation.
+struct df64 {
+  float hi, lo;
+  df64() = default;
+  __device__ df64(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  __device__ explicit df64(unsigned x) {
+    hi = __uint2float_rz(x);                              // at most x, 24 significant bits
+    lo = __uint2float_rn(x - (unsigned)hi);               // the rest is below 2^8: exact
+  }
+  __device__ df64(float h, float l) : hi(h), lo(l) {}
+  __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ df64 df_norm(float s, float e) {  // |s| >= |e| (or s = 0)
+  const float h = __fadd_rn(s, e);
+  return df64(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return df_norm(s, e);
+}
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+__device__ __forceinline__ df64& operator+=(df64& a, df64 b) { a = a + b; return a; }
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_norm(p, e);
+}
+__device__ __forceinline__ df64 fmaF(df64 a, df64 b, df64 c) {  // a b + c
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float s = __fadd_rn(p, c.hi);
+  const float bb = __fsub_rn(s, p);
+  float t = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(c.hi, bb));
+  t = __fadd_rn(t, __fadd_rn(e, c.lo));
+  return df_norm(s, t);
+}
+__device__ __forceinline__ bool operator>(df64 a, df64 b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__device__ __forceinline__ bool operator<=(df64 a, df64 b) { return !(a > b); }
+using ::__shfl_xor_sync;  // the built-in overloads stay visible beside the double-float ones
+using ::__shfl_up_sync;
+__device__ __forceinline__ df64 __shfl_xor_sync(unsigned mask, df64 v, int o) {
+  return df64(::__shfl_xor_sync(mask, v.hi, o), ::__shfl_xor_sync(mask, v.lo, o));
+}
+__device__ __forceinline__ df64 __shfl_up_sync(unsigned mask, df64 v, unsigned o) {
+  return df64(::__shfl_up_sync(mask, v.hi, o), ::__shfl_up_sync(mask, v.lo, o));
+}
+// 1/d: the correctly rounded FP32 reciprocal x, then one Newton step in double-float,
+// x + x (1 - d x), whose residual is formed exactly enough by fused multiply-adds.
+__device__ __forceinline__ df64 rcpF(df64 d) {
+  const float x = __frcp_rn(d.hi);
+  float r = __fmaf_rn(-d.hi, x, 1.0f);   // exact: 1 - d.hi x
+  r = __fmaf_rn(-d.lo, x, r);
+  return df_norm(x, __fmul_rn(x, r));
+}
 
 // index(i, j) = floor((2 i j + K - 1) / (2 (K - 1))): nearest level to i j / (K - 1).
 // The quotient is < K <= 4096, so a float estimate is within one of it.
@@ -284,7 +356,7 @@ __device__ void class_totals(const ClassPlan& P, const unsigned* csz, const unsi
     F acc = 0;
     for (unsigned c = 0; c < len; ++c) {
       const unsigned cell = cells[c];
-      acc = fma(Rc[cell >> 16], Lc[cell & 0xffffu], acc);
+      acc = fmaF(Rc[cell >> 16], Lc[cell & 0xffffu], acc);
     }
     part[p - pbase] = acc;
   }
@@ -419,7 +491,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     // Eq. 11: class totals P_k of the own classes; q_k = S_k / P_k to every CTA.
     if (warp == NW - 1) {  // meanwhile: the L scale and 1 / denominator of Eq. 13 (every CTA alike)
       F s1 = 0.0, s2 = 0.0;
-      for (int b = lane; b < nL; b += 32) { const F x = L0[b]; s1 += x; s2 = fma(x, x, s2); }
+      for (int b = lane; b < nL; b += 32) { const F x = L0[b]; s1 += x; s2 = fmaF(x, x, s2); }
       for (int o = 16; o > 0; o >>= 1) {
         s1 += __shfl_xor_sync(FULL, s1, o);
         s2 += __shfl_xor_sync(FULL, s2, o);
@@ -427,7 +499,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
       if (lane == 0) {
         const F sl = it == 0 ? 1.0 : N * rcpF(s1);
         scal[3] = sl;
-        scal[0] = rcpF(fma(s2 * (sl * sl), invNN, beta));
+        scal[0] = rcpF(fmaF(s2 * (sl * sl), invNN, beta));
       }
     }
     for (int b = tid; b < nL; b += NT) { const F x = L0[b]; L2c[b] = x * x; }
@@ -453,12 +525,12 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         F acc = 0.0;
         if (a < aB) {
           const int i = RI[a];
-          for (int b = gl; b < nL; b += GA) acc = fma(L2c[b], q[class_index(i, LJ[b], km1, inv_d)], acc);
+          for (int b = gl; b < nL; b += GA) acc = fmaF(L2c[b], q[class_index(i, LJ[b], km1, inv_d)], acc);
         }
         for (int o = GA >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
         if (gl == 0 && a < aB) {
           const F r = scR * R0[a];
-          const F ru = fma(r * invN, acc * sl2, beta * (F)G[RI[a]]) * rdR;
+          const F ru = fmaF(r * invN, acc * sl2, beta * (F)G[RI[a]]) * rdR;
           R1[a] = ru;
           RRc[a] = ru * r;
         }
@@ -474,12 +546,12 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     // Eq. 12 for the own columns: lane groups of GB over the reflectance bins.
     if (warp == NW - 1) {  // meanwhile: 1 / denominator of Eq. 12 and the next R scale N / sum R'
       F s1 = 0.0, s2 = 0.0;
-      for (int a = lane; a < nR; a += 32) { const F x = R1[a]; s1 += x; s2 = fma(x, x, s2); }
+      for (int a = lane; a < nR; a += 32) { const F x = R1[a]; s1 += x; s2 = fmaF(x, x, s2); }
       for (int o = 16; o > 0; o >>= 1) {
         s1 += __shfl_xor_sync(FULL, s1, o);
         s2 += __shfl_xor_sync(FULL, s2, o);
       }
-      if (lane == 0) { scal[1] = rcpF(fma(s2, invNN, alpha)); scal[2] = N * rcpF(s1); }
+      if (lane == 0) { scal[1] = rcpF(fmaF(s2, invNN, alpha)); scal[2] = N * rcpF(s1); }
     }
     {
       F* Bs = L2c;  // column sums (L^2 is not needed again in this iteration)
@@ -489,7 +561,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         F acc = 0.0;
         if (b < bB) {
           const int j = LJ[b];
-          for (int a = gl; a < nR; a += GB) acc = fma(RRc[a], q[class_index(RI[a], j, km1, inv_d)], acc);
+          for (int a = gl; a < nR; a += GB) acc = fmaF(RRc[a], q[class_index(RI[a], j, km1, inv_d)], acc);
         }
         for (int o = GB >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
         if (gl == 0 && b < bB) Bs[b] = acc;
@@ -497,7 +569,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
       __syncthreads();
       if (it == 1) stamp();
       const F rdL = scal[1];
-      for (int b = bA + tid; b < bB; b += NT) L1[b] = fma(scL * L0[b] * invN, Bs[b], alpha * Sd[LJ[b]]) * rdL;
+      for (int b = bA + tid; b < bB; b += NT) L1[b] = fmaF(scL * L0[b] * invN, Bs[b], alpha * Sd[LJ[b]]) * rdL;
     }
     __syncthreads();
     if (it == 1) stamp();
@@ -517,8 +589,8 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
       __syncthreads();
       const F scL1 = scal[4];
       F dr = 0.0, dl = 0.0;
-      for (int a = tid; a < nR; a += NT) { const F d = scR1 * R1[a] - scR * R0[a]; dr = fma(d, d, dr); }
-      for (int b = tid; b < nL; b += NT) { const F d = scL1 * L1[b] - scL * L0[b]; dl = fma(d, d, dl); }
+      for (int a = tid; a < nR; a += NT) { const F d = scR1 * R1[a] - scR * R0[a]; dr = fmaF(d, d, dr); }
+      for (int b = tid; b < nL; b += NT) { const F d = scL1 * L1[b] - scL * L0[b]; dl = fmaF(d, d, dl); }
       for (int o = 16; o > 0; o >>= 1) {
         dr += __shfl_xor_sync(FULL, dr, o);
         dl += __shfl_xor_sync(FULL, dl, o);
@@ -727,7 +799,9 @@ cudaError_t launch_solve_t(const SolveArgs& a, int n, int cluster, cudaStream_t 
 }
 
 cudaError_t launch_solve(const SolveArgs& a, int n, int cluster, cudaStream_t st) {
-  return a.fp32 ? launch_solve_t<float>(a, n, cluster, st) : launch_solve_t<double>(a, n, cluster, st);
+  if (a.arith == kArithF32) return launch_solve_t<float>(a, n, cluster, st);
+  if (a.arith == kArithDF64) return launch_solve_t<df64>(a, n, cluster, st);
+  return launch_solve_t<double>(a, n, cluster, st);
 }
 
 }  // namespace hr

@@ -46,7 +46,8 @@ extern "C" hr_status histretinex_enhance_noalloc(const hr_params* p, const void*
   hr_status s = hr::check_params(p);
   if (s != HR_OK) return s;
   if (p->K > kStaticMaxK) return HR_ERR_UNSUPPORTED;  // the static workspace is sized for K <= 256
-  if (p->precision != HR_PREC_FP64 && p->precision != HR_PREC_FP32) return HR_ERR_INVALID_ARG;
+  if (p->precision != HR_PREC_FP64 && p->precision != HR_PREC_FP32 && p->precision != HR_PREC_DF64)
+    return HR_ERR_INVALID_ARG;
   if (!d_in || !d_out || width < 1 || height < 1 || (elem_bytes != 1 && elem_bytes != 2)) return HR_ERR_INVALID_ARG;
   const size_t row = (size_t)3 * width * elem_bytes;
   if (in_pitch < row || out_pitch < row) return HR_ERR_INVALID_ARG;
@@ -118,7 +119,7 @@ extern "C" hr_status histretinex_enhance_noalloc(const hr_params* p, const void*
   a.status = d_status;
   a.vec_in_smem = 1;
   a.profile = 0;
-  a.fp32 = p->precision == HR_PREC_FP32 ? 1 : 0;
+  a.arith = p->precision == HR_PREC_FP32 ? hr::kArithF32 : (p->precision == HR_PREC_DF64 ? hr::kArithDF64 : hr::kArithF64);
   e = hr::launch_solve(a, 1, 16, st);
   if (e != cudaSuccess) return HR_ERR_CUDA;
   e = hr::launch_apply(d_desc, 1, d_tiles, tiles, elem_bytes, K, base, lay.bytes, lay, d_status, sms * 8, st, fast_out);
