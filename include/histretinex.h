@@ -175,6 +175,12 @@ const char* histretinex_status_string(hr_status s);
 /* Device workspace bytes the context keeps per image of a batch (for memory budgeting). */
 size_t histretinex_workspace_bytes(const hr_ctx* ctx);
 
+/* Allocates now the workspace and descriptor buffers of batches of up to n_images images, so that
+ * later calls with at most that many images allocate nothing (growing them frees the old buffers,
+ * which waits for all work on the device).  Not part of the paper's method: serving support.
+ * HR_ERR_INVALID_ARG for n_images < 1, HR_ERR_OOM when the allocation fails. */
+hr_status histretinex_reserve(hr_ctx* ctx, int n_images);
+
 /* Sets / reads the context's launch shapes (see hr_tuning).  Invalid fields give
  * HR_ERR_INVALID_ARG and leave the tuning unchanged. */
 hr_status histretinex_set_tuning(hr_ctx* ctx, const hr_tuning* t);

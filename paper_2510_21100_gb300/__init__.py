@@ -24,7 +24,7 @@ EXPORTS = (
     "histretinex_enhance_host", "histretinex_get_debug", "histretinex_sync_status", "histretinex_destroy",
     "histretinex_status_string", "histretinex_kernel_launches", "histretinex_stage_times",
     "histretinex_profile_solve", "histretinex_set_tuning", "histretinex_get_tuning",
-    "histretinex_workspace_bytes", "histretinex_enhance_noalloc",
+    "histretinex_workspace_bytes", "histretinex_enhance_noalloc", "histretinex_reserve",
 )
 
 
@@ -93,6 +93,8 @@ def _lib():
         L.histretinex_get_tuning.restype = ctypes.c_int
         L.histretinex_enhance_noalloc.argtypes = [ctypes.POINTER(hr_params), vp, vp, i, i, sz, sz, i, vp]
         L.histretinex_enhance_noalloc.restype = ctypes.c_int
+        L.histretinex_reserve.argtypes = [vp, i]
+        L.histretinex_reserve.restype = ctypes.c_int
         L.histretinex_workspace_bytes.argtypes = [vp]
         L.histretinex_workspace_bytes.restype = ctypes.c_size_t
         for name in ("histretinex_create", "histretinex_enhance", "histretinex_enhance_batch",
@@ -322,6 +324,10 @@ class Context:
         n = ctypes.c_int(48)
         _check(_lib().histretinex_profile_solve(self._h, image, buf, ctypes.byref(n)), "histretinex_profile_solve")
         return list(buf[: n.value])
+
+    def reserve(self, n_images: int) -> None:
+        """Allocates the workspace for batches of up to n_images now (later calls then allocate nothing)."""
+        _check(_lib().histretinex_reserve(self._h, int(n_images)), "histretinex_reserve")
 
     def kernel_launches(self) -> int:
         return int(_lib().histretinex_kernel_launches(self._h))

@@ -115,7 +115,7 @@ SlotLayout make_layout(int K) {
   o = align256(o);
   L.cls = o; o += (size_t)4 * K * 4;
   o = align256(o);
-  L.list = o; o += (size_t)K * K * 4;
+  L.list = o; o += (size_t)K * (K + 1) * 4;  // class-major cell lists; later the Eq. 19 row segments
   o = align256(o);
   L.max_pieces = (size_t)K * K / kPiece + K;
   L.piece = o; o += L.max_pieces * 8;
@@ -223,7 +223,6 @@ cudaError_t enqueue_stages(hr_ctx* c, int n, int total, int units, int elem_byte
   a.slot_bytes = c->lay.bytes;
   a.lay = c->lay;
   a.status = c->d_status;
-  a.vec_in_smem = K <= 1024 ? 1 : 0;
   a.profile = (c->p.flags & HR_FLAG_DEBUG_OUT) ? 1 : 0;
   a.arith = c->p.precision == HR_PREC_FP32 ? hr::kArithF32 : (c->p.precision == HR_PREC_DF64 ? hr::kArithDF64 : hr::kArithF64);
   e = hr::launch_solve(a, n, batched ? 1 : c->tune.solve_cluster, st);
@@ -516,6 +515,14 @@ const char* histretinex_status_string(hr_status s) {
 }
 
 size_t histretinex_workspace_bytes(const hr_ctx* c) { return c ? c->lay.bytes : 0; }
+
+hr_status histretinex_reserve(hr_ctx* c, int n_images) {
+  if (!c || n_images < 1) return HR_ERR_INVALID_ARG;
+  HR_CUDA(cudaSetDevice(c->device));
+  hr_status s = ensure_slots(c, n_images);
+  if (s != HR_OK) return s;
+  return ensure_desc(c, n_images);
+}
 
 hr_status histretinex_set_tuning(hr_ctx* c, const hr_tuning* t) {
   if (!c || !t) return HR_ERR_INVALID_ARG;

@@ -40,7 +40,8 @@ struct SlotLayout {
   size_t misc;          // int[4]: iterations, nR, nL, cells; then long long[kProfSlots] phase times
   size_t vec;           // solver vectors when they do not fit in shared memory
   size_t cls;           // uint32[4*K]: class size, cell start, first piece, piece count
-  size_t list;          // uint32[K*K]: class-major cell list, (a << 16) | b
+  size_t list;          // uint32[K*(K+1)]: class-major cell lists, (a << 16) | b; then the
+                        // Eq. 19 row segments (at most K (K+1) / 2 solver values)
   size_t piece;         // uint2[max_pieces]: (cell start, len | class << 16)
   size_t part;          // double[max_parts]: piece partial sums
   size_t bytes;         // total slot size (multiple of 256)
@@ -71,7 +72,8 @@ struct SolveArgs {
   size_t slot_bytes;
   SlotLayout lay;
   unsigned* status;
-  int vec_in_smem;           // 1: solver vectors in dynamic shared memory
+  int vec_in_smem;           // 1: solver vectors in dynamic shared memory (set by launch_solve)
+  int list_in_smem;          // 1: own cell lists may use shared memory (set by launch_solve)
   int profile;               // 1: record phase timestamps into the slot's misc area
   int arith;                 // kArithF64 (plain form), kArithF32 (reduced precision), kArithDF64
 };
@@ -88,7 +90,7 @@ cudaError_t launch_solve(const SolveArgs& a, int n, int cluster, cudaStream_t st
 cudaError_t launch_apply(const ImageDesc* d_imgs, int n, const int* d_tile_start, int total_tiles, int elem_bytes,
                          int K, uint8_t* slots, size_t slot_bytes, SlotLayout lay, unsigned* status, int grid,
                          cudaStream_t st, bool fast);
-size_t solve_smem_bytes(int K, int vec_in_smem, size_t fsize);
+size_t solve_smem_bytes(int K, int vec_in_smem, int list_in_smem, size_t fsize);
 
 // Geometry of the pixel passes: tiles of kTileW x kTileH pixels.
 constexpr int kTileW = 128;

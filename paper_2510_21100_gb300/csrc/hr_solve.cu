@@ -104,13 +104,9 @@ __device__ __forceinline__ df64 fmaF(df64 a, df64 b, df64 c) {  // a b + c
 }
 __device__ __forceinline__ bool operator>(df64 a, df64 b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
 __device__ __forceinline__ bool operator<=(df64 a, df64 b) { return !(a > b); }
-using ::__shfl_xor_sync;  // the built-in overloads stay visible beside the double-float ones
-using ::__shfl_up_sync;
+using ::__shfl_xor_sync;  // the built-in overloads stay visible beside the double-float one
 __device__ __forceinline__ df64 __shfl_xor_sync(unsigned mask, df64 v, int o) {
   return df64(::__shfl_xor_sync(mask, v.hi, o), ::__shfl_xor_sync(mask, v.lo, o));
-}
-__device__ __forceinline__ df64 __shfl_up_sync(unsigned mask, df64 v, unsigned o) {
-  return df64(::__shfl_up_sync(mask, v.hi, o), ::__shfl_up_sync(mask, v.lo, o));
 }
 // 1/d: the correctly rounded FP32 reciprocal x, then one Newton step in double-float,
 // x + x (1 - d x), whose residual is formed exactly enough by fused multiply-adds.
@@ -303,7 +299,7 @@ __device__ ClassPlan plan_classes(const cg::cluster_group& cl, int nR, int ncls,
   P.pB = P.cB < ncls ? pst[P.cB] : npieces;
   P.cell0 = P.cA < ncls ? cst[P.cA] : P.cells;
   const unsigned cell1 = P.cB < ncls ? cst[P.cB] : P.cells;
-  if (cell1 - P.cell0 <= (unsigned)kListCap && P.pB - P.pA <= (unsigned)kPieceCap) {
+  if (ob.s_list && cell1 - P.cell0 <= (unsigned)kListCap && P.pB - P.pA <= (unsigned)kPieceCap) {
     P.listp = ob.s_list; P.piecep = ob.s_piece; P.partp = ob.s_part;
   } else {
     P.listp = ob.g_list; P.piecep = ob.g_piece; P.partp = ob.g_part;  // whole-image indexing
@@ -421,9 +417,12 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   unsigned* ured = reinterpret_cast<unsigned*>(smem + off); off += ((NW + 2) * sizeof(unsigned) + 15) & ~(size_t)15;
   double* scr = reinterpret_cast<double*>(smem + off); off += NT * sizeof(double);   // LUT scans
   OwnBufs ob;
-  ob.s_part = smem + off; off += (size_t)kPieceCap * sizeof(F);
-  ob.s_piece = reinterpret_cast<uint2*>(smem + off); off += (size_t)kPieceCap * sizeof(uint2);
-  ob.s_list = reinterpret_cast<unsigned*>(smem + off); off += (size_t)kListCap * sizeof(unsigned);
+  ob.s_part = nullptr; ob.s_piece = nullptr; ob.s_list = nullptr;
+  if (A.list_in_smem) {  // (large K: the lists exceed any shared-memory share, so none is reserved)
+    ob.s_part = smem + off; off += (size_t)kPieceCap * sizeof(F);
+    ob.s_piece = reinterpret_cast<uint2*>(smem + off); off += (size_t)kPieceCap * sizeof(uint2);
+    ob.s_list = reinterpret_cast<unsigned*>(smem + off); off += (size_t)kListCap * sizeof(unsigned);
+  }
   ob.g_list = reinterpret_cast<unsigned*>(slot + lay.list);
   ob.g_piece = reinterpret_cast<uint2*>(slot + lay.piece);
   ob.g_part = slot + lay.part;
@@ -624,14 +623,64 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   Lc = L1;
 
   // ---- Eq. 17-20: enhanced histogram through the index_1 class map -----------------------------
-  F* T = L2c;  // level-indexed target, filled by every CTA's own classes
-  for (int k = tid; k < K; k += NT) T[k] = 0.0;
-  const ClassPlan PT = plan_classes(cl, nR, K, RI, posL, JsTable{A.jstart1, K}, [](int c) { return c; }, csz, cst,
-                                    pst, ob, ured, rank, C);  // (its cluster barrier orders the zeroing)
+  // The cells of class k in row i (Eq. 19) are the support columns of [js1(i, k), js1(i, k+1)),
+  // so T_k = (1/N) sum_i R_i (sum of L over that run).  Row i meets the classes [k0, k1] of its
+  // first and last support column (index_1 grows with j).  Row pass: R_i times every run sum into
+  // the row's segment of the workspace (own rows); class pass: T_k as the sum over the rows whose
+  // range holds k, rows ascending (own classes).
+  const JsTable js1{A.jstart1, K};
+  unsigned* rk0 = csz;   // per row: first class (the class-plan arrays are free by now)
+  unsigned* rk1 = cst;   // per row: last class
+  unsigned* roff = pst;  // per row: segment offset in the workspace
+  {
+    const int jmin = LJ[0], jmax = LJ[nL - 1];
+    for (int a = tid; a < nR; a += NT) {
+      const int i = RI[a];
+      auto cls_of = [&](int j) {  // class of column j in row i: the last k with js1(i, k) <= j
+        int lo = 0, hi = K - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (js1(i, mid) <= j) lo = mid; else hi = mid - 1;
+        }
+        return lo;
+      };
+      const int k0 = cls_of(jmin), k1 = cls_of(jmax);
+      rk0[a] = (unsigned)k0;
+      rk1[a] = (unsigned)k1;
+      roff[a] = (unsigned)(k1 - k0 + 1);  // at most i + 1: the segments fit K (K + 1) / 2 entries
+    }
+    __syncthreads();
+    block_exscan_array(roff, nR, ured);
+  }
+  F* seg = reinterpret_cast<F*>(slot + lay.list);
+  for (int a = aA + warp; a < aB; a += NW) {
+    const int i = RI[a];
+    const F r = Rc[a];
+    const int k0 = (int)rk0[a], k1 = (int)rk1[a];
+    F* out = seg + roff[a];
+    for (int k = k0 + lane; k <= k1; k += 32) {
+      const int p0 = posL[js1(i, k)], p1 = posL[js1(i, k + 1)];
+      F sum = 0.0;
+      for (int b = p0; b < p1; ++b) sum += Lc[b];
+      out[k - k0] = r * sum;
+    }
+  }
+  __threadfence();  // the segments are read by every CTA of the cluster
+  cl.sync();
   stamp();
-  class_totals<F>(PT, csz, pst, Rc, Lc, [&](int c, F s) { T[c] = s * invN; });  // count matrix carries 1/N (Eq. 6)
-  __syncthreads();
-  push_slice(cl, T, PT.cA, PT.cB, C, rank);
+  F* T = L2c;  // level-indexed target
+  {
+    const int kA = (int)((long long)K * rank / C), kB = (int)((long long)K * (rank + 1) / C);
+    for (int k = kA + warp; k < kB; k += NW) {
+      F sum = 0.0;
+      for (int a = lane; a < nR; a += 32)
+        if ((int)rk0[a] <= k && k <= (int)rk1[a]) sum += seg[roff[a] + (unsigned)(k - (int)rk0[a])];
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+      if (lane == 0) T[k] = sum * invN;  // the count matrix carries 1/N (Eq. 6)
+    }
+    __syncthreads();
+    push_slice(cl, T, kA, kB, C, rank);
+  }
   cl.sync();
   stamp();
   if (rank != 0) return;
@@ -735,16 +784,19 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
 
 }  // namespace
 
-size_t solve_smem_bytes(int K, int vec_in_smem, size_t fsize) {
+size_t solve_smem_bytes(int K, int vec_in_smem, int list_in_smem, size_t fsize) {
   size_t off = ((size_t)(3 * K + 1) * sizeof(uint16_t) + 15) & ~(size_t)15;
   off += (size_t)3 * K * 4;
   off += 8 * sizeof(double);
   off += ((NW + 2) * sizeof(unsigned) + 15) & ~(size_t)15;
   off += NT * sizeof(double);
-  off += (size_t)kPieceCap * (fsize + sizeof(uint2)) + (size_t)kListCap * sizeof(unsigned);
+  if (list_in_smem) off += (size_t)kPieceCap * (fsize + sizeof(uint2)) + (size_t)kListCap * sizeof(unsigned);
   if (vec_in_smem) off += (size_t)kSolveVecs * K * fsize;
   return off;
 }
+
+// Shared memory one CTA may use (sm_103a: 227 KB).
+constexpr size_t kSmemMax = 227 * 1024;
 
 // Largest cluster (16, 8, 4, 2 or 1 CTAs) of solve_kernel<F> that can be resident for one image.
 template <typename F>
@@ -769,8 +821,13 @@ int solve_cluster_size(size_t smem) {
 }
 
 template <typename F>
-cudaError_t launch_solve_t(const SolveArgs& a, int n, int cluster, cudaStream_t st) {
-  const size_t smem = solve_smem_bytes(a.K, a.vec_in_smem, sizeof(F));
+cudaError_t launch_solve_t(const SolveArgs& a0, int n, int cluster, cudaStream_t st) {
+  // own cell lists in shared memory up to K = 1024 (beyond it they never fit a share); the
+  // solver vectors there whenever the layout fits (for K = 4096: FP32 only)
+  SolveArgs a = a0;
+  a.list_in_smem = a.K <= 1024 ? 1 : 0;
+  a.vec_in_smem = solve_smem_bytes(a.K, 1, a.list_in_smem, sizeof(F)) <= kSmemMax ? 1 : 0;
+  const size_t smem = solve_smem_bytes(a.K, a.vec_in_smem, a.list_in_smem, sizeof(F));
   cudaError_t e = cudaFuncSetAttribute(solve_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(solve_kernel<F>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

@@ -117,7 +117,6 @@ extern "C" hr_status histretinex_enhance_noalloc(const hr_params* p, const void*
   a.slot_bytes = lay.bytes;
   a.lay = lay;
   a.status = d_status;
-  a.vec_in_smem = 1;
   a.profile = 0;
   a.arith = p->precision == HR_PREC_FP32 ? hr::kArithF32 : (p->precision == HR_PREC_DF64 ? hr::kArithDF64 : hr::kArithF64);
   e = hr::launch_solve(a, 1, 16, st);

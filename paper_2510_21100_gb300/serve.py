@@ -65,6 +65,11 @@ class Server:
         self.device = device
         self.streams = [torch.cuda.Stream(device=device) for _ in range(streams)]
         self.ctxs = [hr.Context(self.params, device=device) for _ in range(streams)]
+        for c in self.ctxs:
+            # each batch has its own geometry, so a captured graph would never be replayed; and the
+            # workspace of the largest batch is allocated now, not while requests wait
+            c.set_tuning(use_graph=0)
+            c.reserve(max_batch)
         self.slot_bytes = self.ctxs[0].workspace_bytes()  # library workspace per admitted image
 
     def _need(self, req: Request) -> int:

@@ -146,3 +146,19 @@ def test_server_respects_the_memory_budget(hr):
     st = srv2.run(reqs)
     assert st.completed == 6 and st.max_batch <= 2
     srv.close(); srv2.close()
+
+
+def test_reserve_then_batches_up_to_the_reserved_size(hr):
+    """histretinex_reserve sizes the workspace up front; batches up to that size then run as usual."""
+    import torch
+    import paper_2510_21100_gb300 as hrm
+    ctx = hrm.Context(hrm.Params())
+    ctx.reserve(4)
+    imgs = [torch.from_numpy(synth.low_light_image(64 + 16 * i, 48, seed=600 + i)).cuda() for i in range(4)]
+    ref = [ctx.enhance(x) for x in imgs]
+    outs = ctx.enhance_batch(imgs)
+    ctx.check()
+    for a, b in zip(ref, outs):
+        assert torch.equal(a, b)
+    with pytest.raises(hrm.HistRetinexError):
+        ctx.reserve(0)
