@@ -223,16 +223,30 @@ __device__ __forceinline__ void push_slice(const cg::cluster_group& cl, T* arr, 
   }
 }
 
-// Same for the entries arr[map[c]], c in [lo, hi).
+// Pull forms of the exchanges: after the cluster barrier that published the owners' entries, each
+// CTA reads the entries it does not own straight from the owner's shared memory (one remote load
+// per entry, all in flight together), instead of every owner storing into every peer before the
+// barrier (remote stores before a barrier cost far more than remote loads after it on GB300).
+// arr[map[c]] for c in [0, n), owned by owner[c].
 template <typename T>
-__device__ __forceinline__ void push_mapped(const cg::cluster_group& cl, T* arr, const uint16_t* map, int lo, int hi,
-                                            int C, int rank) {
-  const int n = hi - lo;
-  if (C == 1 || n <= 0) return;
-  for (int t = threadIdx.x; t < n * (C - 1); t += NT) {
-    const int r0 = t / n, idx = map[lo + (t - r0 * n)];
-    const int r = r0 >= rank ? r0 + 1 : r0;
-    cl.map_shared_rank(arr, r)[idx] = arr[idx];
+__device__ __forceinline__ void pull_mapped(const cg::cluster_group& cl, T* arr, const uint16_t* map, int n,
+                                            const uint8_t* owner, int C, int rank) {
+  if (C == 1) return;
+  for (int c = threadIdx.x; c < n; c += NT) {
+    const int r = owner[c];
+    if (r != rank) {
+      const int idx = map[c];
+      arr[idx] = cl.map_shared_rank(arr, r)[idx];
+    }
+  }
+}
+// arr[0, n) split evenly: rank r owns [floor(n r / C), floor(n (r + 1) / C)).
+template <typename T>
+__device__ __forceinline__ void pull_even(const cg::cluster_group& cl, T* arr, int n, int C, int rank) {
+  if (C == 1) return;
+  for (int a = threadIdx.x; a < n; a += NT) {
+    const int r = ((a + 1) * C - 1) / n;
+    if (r != rank) arr[a] = cl.map_shared_rank(arr, r)[a];
   }
 }
 
@@ -416,6 +430,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   F* scal = reinterpret_cast<F*>(smem + off); off += 8 * sizeof(double);  // per-iteration scalars
   unsigned* ured = reinterpret_cast<unsigned*>(smem + off); off += ((NW + 2) * sizeof(unsigned) + 15) & ~(size_t)15;
   double* scr = reinterpret_cast<double*>(smem + off); off += NT * sizeof(double);   // LUT scans
+  uint8_t* cowner = reinterpret_cast<uint8_t*>(smem + off); off += ((size_t)K + 15) & ~(size_t)15;  // class -> CTA
   OwnBufs ob;
   ob.s_part = nullptr; ob.s_piece = nullptr; ob.s_list = nullptr;
   if (A.list_in_smem) {  // (large K: the lists exceed any shared-memory share, so none is reserved)
@@ -467,6 +482,13 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   const ClassPlan PP = plan_classes(cl, nR, nL, RI, posL, JsIndex{K}, [&](int c) { return (int)LJ[c]; }, csz, cst,
                                     pst, ob, ured, rank, C);
   stamp();
+  // owner CTA of every class of the plan: rank r holds the classes whose first cell lies in
+  // [cells r / C, cells (r + 1) / C) (rank 0 also those below, the last rank those above)
+  for (int c = tid; c < nL; c += NT) {
+    int r = C - 1;
+    while (r > 0 && cst[c] < (unsigned)(((unsigned long long)PP.cells * r) / C)) --r;
+    cowner[c] = (uint8_t)r;
+  }
   // own rows and columns of the updates (contiguous slices)
   const int aA = (int)((long long)nR * rank / C), aB = (int)((long long)nR * (rank + 1) / C);
   const int bA = (int)((long long)nL * rank / C), bB = (int)((long long)nL * (rank + 1) / C);
@@ -510,8 +532,9 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     });
     __syncthreads();
     if (it == 1) stamp();
-    push_mapped(cl, q, LJ, PP.cA, PP.cB, C, rank);
     cl.sync();
+    pull_mapped(cl, q, LJ, nL, cowner, C, rank);
+    __syncthreads();
     scL = scal[3];
     if (it <= 1) stamp();
 
@@ -537,9 +560,10 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     }
     __syncthreads();
     if (it == 1) stamp();
-    push_slice(cl, R1, aA, aB, C, rank);
-    push_slice(cl, RRc, aA, aB, C, rank);
     cl.sync();
+    pull_even(cl, R1, nR, C, rank);
+    pull_even(cl, RRc, nR, C, rank);
+    __syncthreads();
     if (it <= 1) stamp();
 
     // Eq. 12 for the own columns: lane groups of GB over the reflectance bins.
@@ -572,8 +596,9 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     }
     __syncthreads();
     if (it == 1) stamp();
-    push_slice(cl, L1, bA, bB, C, rank);
     cl.sync();
+    pull_even(cl, L1, nL, C, rank);
+    __syncthreads();
     if (it <= 1) stamp();
 
     const F scR1 = scal[2];
@@ -625,45 +650,42 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   // ---- Eq. 17-20: enhanced histogram through the index_1 class map -----------------------------
   // The cells of class k in row i (Eq. 19) are the support columns of [js1(i, k), js1(i, k+1)),
   // so T_k = (1/N) sum_i R_i (sum of L over that run).  Row i meets the classes [k0, k1] of its
-  // first and last support column (index_1 grows with j).  Row pass: R_i times every run sum into
-  // the row's segment of the workspace (own rows); class pass: T_k as the sum over the rows whose
-  // range holds k, rows ascending (own classes).
+  // first and last support column (index_1 grows with j, and is at most i).  Row pass: R_i times
+  // every run sum into the row's segment of the workspace (own rows; the class ranges go to every
+  // CTA); class pass: T_k as the sum over the rows whose range holds k, rows ascending (own classes).
   const JsTable js1{A.jstart1, K};
   unsigned* rk0 = csz;   // per row: first class (the class-plan arrays are free by now)
   unsigned* rk1 = cst;   // per row: last class
-  unsigned* roff = pst;  // per row: segment offset in the workspace
+  F* seg = reinterpret_cast<F*>(slot + lay.list);  // row i's segment at i (i + 1) / 2, indexed by class
   {
     const int jmin = LJ[0], jmax = LJ[nL - 1];
-    for (int a = tid; a < nR; a += NT) {
+    for (int a = aA + warp; a < aB; a += NW) {  // own rows, a warp each
       const int i = RI[a];
-      auto cls_of = [&](int j) {  // class of column j in row i: the last k with js1(i, k) <= j
-        int lo = 0, hi = K - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (js1(i, mid) <= j) lo = mid; else hi = mid - 1;
-        }
-        return lo;
-      };
-      const int k0 = cls_of(jmin), k1 = cls_of(jmax);
-      rk0[a] = (unsigned)k0;
-      rk1[a] = (unsigned)k1;
-      roff[a] = (unsigned)(k1 - k0 + 1);  // at most i + 1: the segments fit K (K + 1) / 2 entries
+      // classes of the first and last support column: k0 + 1 = #{k : js1(i, k) <= jmin}, likewise
+      // k1 for jmax (js1 grows with k; boundaries read 32 at a time, counted by ballots)
+      int c0 = 0, c1 = 0;
+      for (int kb = 0; kb < K; kb += 32) {
+        const int k = kb + lane;
+        const int v = k < K ? js1(i, k) : K + 1;
+        const unsigned m1 = __ballot_sync(FULL, v <= jmax);
+        c0 += __popc(__ballot_sync(FULL, v <= jmin));
+        c1 += __popc(m1);
+        if (m1 != FULL) break;  // the boundaries have passed the last support column
+      }
+      const int k0 = c0 - 1, k1 = min(c1 - 1, i);  // (index_1 never exceeds i: a_j <= 1)
+      if (lane == 0) { rk0[a] = (unsigned)k0; rk1[a] = (unsigned)k1; }
+      const F r = Rc[a];
+      F* out = seg + (size_t)i * (i + 1) / 2;  // row i meets at most classes 0 .. i
+      for (int k = k0 + lane; k <= k1; k += 32) {
+        const int p0 = posL[js1(i, k)], p1 = posL[js1(i, k + 1)];
+        F sum = 0.0;
+        for (int b = p0; b < p1; ++b) sum += Lc[b];
+        out[k] = r * sum;
+      }
     }
     __syncthreads();
-    block_exscan_array(roff, nR, ured);
-  }
-  F* seg = reinterpret_cast<F*>(slot + lay.list);
-  for (int a = aA + warp; a < aB; a += NW) {
-    const int i = RI[a];
-    const F r = Rc[a];
-    const int k0 = (int)rk0[a], k1 = (int)rk1[a];
-    F* out = seg + roff[a];
-    for (int k = k0 + lane; k <= k1; k += 32) {
-      const int p0 = posL[js1(i, k)], p1 = posL[js1(i, k + 1)];
-      F sum = 0.0;
-      for (int b = p0; b < p1; ++b) sum += Lc[b];
-      out[k - k0] = r * sum;
-    }
+    push_slice(cl, rk0, aA, aB, C, rank);
+    push_slice(cl, rk1, aA, aB, C, rank);
   }
   __threadfence();  // the segments are read by every CTA of the cluster
   cl.sync();
@@ -674,7 +696,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     for (int k = kA + warp; k < kB; k += NW) {
       F sum = 0.0;
       for (int a = lane; a < nR; a += 32)
-        if ((int)rk0[a] <= k && k <= (int)rk1[a]) sum += seg[roff[a] + (unsigned)(k - (int)rk0[a])];
+        if ((int)rk0[a] <= k && k <= (int)rk1[a]) sum += seg[(size_t)RI[a] * (RI[a] + 1) / 2 + k];
       for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
       if (lane == 0) T[k] = sum * invN;  // the count matrix carries 1/N (Eq. 6)
     }
@@ -713,6 +735,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     const double before = ex + (warp > 0 ? scr[NW + warp - 1] : 0.0);
     for (int k = b0; k < b1; ++k) CT[k] += before;
     __syncthreads();
+    stamp();
     const double TT = CT[K - 1];
     // non-negative doubles order like their bit patterns; a running max makes lhs monotone so the
     // first z with lhs(z) >= rhs(s) is found by binary search
@@ -745,6 +768,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     unsigned long long pm = warp > 0 ? wmax[NW + warp - 1] : 0ull;
     if (exm > pm) pm = exm;
     for (int k = b0; k < b1; ++k) lhs[k] = lhs[k] > pm ? lhs[k] : pm;
+    stamp();
     // z_top: last occupied target level.  Where CS(s) = N the matching condition reads
     // CT(z) >= TT, which in exact arithmetic first holds at z_top; that level is used directly.
     int top_local = -1;
@@ -759,6 +783,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     unsigned cs_total;
     unsigned cs = block_exscan(cs_local, ured, &cs_total);  // (synchronises: ztop and lhs are final)
     const int z_top = (int)*ztop;
+    stamp();
     for (int k = b0; k < b1; ++k) {
       cs += S[k];
       if (cs == Nu) { lut[k] = (uint16_t)z_top; continue; }
@@ -772,6 +797,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     }
   }
   __syncthreads();
+  stamp();
 
   // ---- results (level-indexed) -------------------------------------------------------------------
   for (int k = tid; k < K; k += NT) { Rout[k] = 0.0; Lout[k] = 0.0; Tout[k] = (double)T[k]; }
@@ -790,6 +816,7 @@ size_t solve_smem_bytes(int K, int vec_in_smem, int list_in_smem, size_t fsize) 
   off += 8 * sizeof(double);
   off += ((NW + 2) * sizeof(unsigned) + 15) & ~(size_t)15;
   off += NT * sizeof(double);
+  off += ((size_t)K + 15) & ~(size_t)15;
   if (list_in_smem) off += (size_t)kPieceCap * (fsize + sizeof(uint2)) + (size_t)kListCap * sizeof(unsigned);
   if (vec_in_smem) off += (size_t)kSolveVecs * K * fsize;
   return off;
