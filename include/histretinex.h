@@ -136,6 +136,17 @@ hr_status histretinex_enhance_batch(hr_ctx* ctx, int n, const void* const* d_in,
 hr_status histretinex_enhance_host(hr_ctx* ctx, const void* h_in, void* h_out, int width, int height,
                                    size_t in_pitch, size_t out_pitch, int elem_bytes, void* stream);
 
+/* End-to-end form for a sequence of n HOST images (arrays of n pointers, sizes and pitches; the
+ * images may differ in size): each image goes through the plain single-image pipeline of
+ * histretinex_enhance, while the host-to-device copy of the next image and the device-to-host
+ * copy of the previous one run on the context's own copy streams (two device buffer pairs, in
+ * turn).  Work already queued on `stream` comes first; the call returns when every result is in
+ * host memory.  Pinned host memory gives full copy speed.  Not part of the paper's method:
+ * throughput support for host-resident images.  Errors as histretinex_enhance_host. */
+hr_status histretinex_enhance_host_many(hr_ctx* ctx, int n, const void* const* h_in, void* const* h_out,
+                                        const int* width, const int* height, const size_t* in_pitch,
+                                        const size_t* out_pitch, int elem_bytes, void* stream);
+
 /* Allocation-free single-image enhancement, without a context.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory at the point of the
  * call -- code running while a framework captures a CUDA graph, real-time loops that must not

@@ -25,6 +25,7 @@ EXPORTS = (
     "histretinex_status_string", "histretinex_kernel_launches", "histretinex_stage_times",
     "histretinex_profile_solve", "histretinex_set_tuning", "histretinex_get_tuning",
     "histretinex_workspace_bytes", "histretinex_enhance_noalloc", "histretinex_reserve",
+    "histretinex_enhance_host_many",
 )
 
 
@@ -76,6 +77,9 @@ def _lib():
         L.histretinex_enhance_batch.argtypes = [vp, i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i),
                                                 ctypes.POINTER(i), ctypes.POINTER(sz), ctypes.POINTER(sz), i, vp]
         L.histretinex_enhance_host.argtypes = [vp, vp, vp, i, i, sz, sz, i, vp]
+        L.histretinex_enhance_host_many.argtypes = [vp, i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i),
+                                                    ctypes.POINTER(i), ctypes.POINTER(sz), ctypes.POINTER(sz), i, vp]
+        L.histretinex_enhance_host_many.restype = ctypes.c_int
         L.histretinex_get_debug.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, ctypes.POINTER(i)]
         L.histretinex_sync_status.argtypes = [vp, vp]
         L.histretinex_destroy.argtypes = [vp]
@@ -273,6 +277,25 @@ class Context:
         _check(_lib().histretinex_enhance_host(self._h, ctypes.c_void_p(pi), ctypes.c_void_p(po), W, H, pin, pout, eb,
                                                _stream_ptr(stream)), "histretinex_enhance_host")
         return h_out
+
+    def enhance_host_many(self, h_ins, h_outs=None, stream=None):
+        """A sequence of host images ((pinned) CPU tensors (H, W, 3), one element size), each through the
+        plain pipeline, with host-device copies overlapped with the neighbouring images' compute."""
+        n = len(h_ins)
+        if h_outs is None:
+            h_outs = [x.new_empty(x.shape) for x in h_ins]
+        geo = [_geom(x) for x in h_ins]
+        geo_o = [_geom(x) for x in h_outs]
+        eb = geo[0][3]
+        if any(g[3] != eb for g in geo):
+            raise ValueError("all images of one call need the same element size")
+        arr = lambda t, v: (t * n)(*v)
+        _check(_lib().histretinex_enhance_host_many(
+            self._h, n, arr(ctypes.c_void_p, [x.data_ptr() for x in h_ins]),
+            arr(ctypes.c_void_p, [x.data_ptr() for x in h_outs]), arr(ctypes.c_int, [g[0] for g in geo]),
+            arr(ctypes.c_int, [g[1] for g in geo]), arr(ctypes.c_size_t, [g[2] for g in geo]),
+            arr(ctypes.c_size_t, [g[2] for g in geo_o]), eb, _stream_ptr(stream)), "histretinex_enhance_host_many")
+        return h_outs
 
     def sync_status(self, stream=None):
         return _lib().histretinex_sync_status(self._h, _stream_ptr(stream))

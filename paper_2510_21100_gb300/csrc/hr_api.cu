@@ -1,6 +1,7 @@
 // C ABI of the HistRetinex CUDA library: context, workspace, per-K tables, launches.
 #include <cmath>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -30,6 +31,12 @@ struct hr_ctx {
   void* d_io_in = nullptr;         // device copies for the host-buffer entry point
   void* d_io_out = nullptr;
   size_t io_bytes = 0;
+  // host-image sequences: two device buffer pairs, a copy stream each way, per-buffer events
+  void* d_pp_in[2] = {nullptr, nullptr};
+  void* d_pp_out[2] = {nullptr, nullptr};
+  size_t pp_bytes = 0;
+  cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+  cudaEvent_t ev_in_ready[2] = {}, ev_in_free[2] = {}, ev_done[2] = {}, ev_out_free[2] = {};
   uint64_t launches = 0;
   int last_n = 0;
   // stage timing: a ring of event quadruples, folded into the sums when reused or queried
@@ -327,6 +334,14 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
   return HR_OK;
 }
 
+// Host-device copy of `height` rows: one flat copy when both sides are contiguous (flat copies in
+// the two directions overlap on GB300; pitched ones measured no overlap), else a pitched copy.
+cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch, size_t row, size_t height,
+                      cudaMemcpyKind kind, cudaStream_t st) {
+  if (dpitch == row && spitch == row) return cudaMemcpyAsync(dst, src, row * height, kind, st);
+  return cudaMemcpy2DAsync(dst, dpitch, src, spitch, row, height, kind, st);
+}
+
 }  // namespace
 
 extern "C" {
@@ -412,12 +427,83 @@ hr_status histretinex_enhance_host(hr_ctx* c, const void* h_in, void* h_out, int
     HR_CUDA(cudaMalloc(&c->d_io_out, bytes));
     c->io_bytes = bytes;
   }
-  HR_CUDA(cudaMemcpy2DAsync(c->d_io_in, dpitch, h_in, in_pitch, row, (size_t)height, cudaMemcpyHostToDevice, st));
+  HR_CUDA(copy_rows(c->d_io_in, dpitch, h_in, in_pitch, row, (size_t)height, cudaMemcpyHostToDevice, st));
   ImageDesc d{static_cast<const uint8_t*>(c->d_io_in), static_cast<uint8_t*>(c->d_io_out), width, height,
               (long long)dpitch, (long long)dpitch};
   hr_status s = run_pipeline(c, 1, &d, elem_bytes, st, false);
   if (s != HR_OK) return s;
-  HR_CUDA(cudaMemcpy2DAsync(h_out, out_pitch, c->d_io_out, dpitch, row, (size_t)height, cudaMemcpyDeviceToHost, st));
+  HR_CUDA(copy_rows(h_out, out_pitch, c->d_io_out, dpitch, row, (size_t)height, cudaMemcpyDeviceToHost, st));
+  return histretinex_sync_status(c, stream);
+}
+
+hr_status histretinex_enhance_host_many(hr_ctx* c, int n, const void* const* h_in, void* const* h_out,
+                                        const int* width, const int* height, const size_t* in_pitch,
+                                        const size_t* out_pitch, int elem_bytes, void* stream) {
+  if (!c || n < 1 || !h_in || !h_out || !width || !height || !in_pitch || !out_pitch ||
+      (elem_bytes != 1 && elem_bytes != 2))
+    return HR_ERR_INVALID_ARG;
+  size_t need = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!h_in[i] || !h_out[i] || width[i] < 1 || height[i] < 1) return HR_ERR_INVALID_ARG;
+    const size_t row = (size_t)3 * width[i] * elem_bytes;
+    if (in_pitch[i] < row || out_pitch[i] < row) return HR_ERR_INVALID_ARG;
+    need = std::max(need, (row + 15) / 16 * 16 * (size_t)height[i]);
+  }
+  HR_CUDA(cudaSetDevice(c->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!c->s_h2d) {
+    HR_CUDA(cudaStreamCreateWithFlags(&c->s_h2d, cudaStreamNonBlocking));
+    HR_CUDA(cudaStreamCreateWithFlags(&c->s_d2h, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+      HR_CUDA(cudaEventCreateWithFlags(&c->ev_in_ready[b], cudaEventDisableTiming));
+      HR_CUDA(cudaEventCreateWithFlags(&c->ev_in_free[b], cudaEventDisableTiming));
+      HR_CUDA(cudaEventCreateWithFlags(&c->ev_done[b], cudaEventDisableTiming));
+      HR_CUDA(cudaEventCreateWithFlags(&c->ev_out_free[b], cudaEventDisableTiming));
+    }
+  }
+  if (need > c->pp_bytes) {
+    HR_CUDA(cudaDeviceSynchronize());
+    for (int b = 0; b < 2; ++b) {
+      cudaFree(c->d_pp_in[b]); cudaFree(c->d_pp_out[b]);
+      c->d_pp_in[b] = c->d_pp_out[b] = nullptr;
+    }
+    c->pp_bytes = 0;
+    for (int b = 0; b < 2; ++b) {
+      HR_CUDA(cudaMalloc(&c->d_pp_in[b], need));
+      HR_CUDA(cudaMalloc(&c->d_pp_out[b], need));
+    }
+    c->pp_bytes = need;
+  }
+  // everything before this call on the caller's stream comes first
+  HR_CUDA(cudaEventRecord(c->ev_done[0], st));
+  HR_CUDA(cudaStreamWaitEvent(c->s_h2d, c->ev_done[0], 0));
+  HR_CUDA(cudaStreamWaitEvent(c->s_d2h, c->ev_done[0], 0));
+  for (int i = 0; i < n; ++i) {
+    const int b = i & 1;
+    const size_t row = (size_t)3 * width[i] * elem_bytes, dpitch = (row + 15) / 16 * 16;
+    // H2D of image i once the pipeline of image i - 2 has left buffer b
+    if (i >= 2) HR_CUDA(cudaStreamWaitEvent(c->s_h2d, c->ev_in_free[b], 0));
+    HR_CUDA(copy_rows(c->d_pp_in[b], dpitch, h_in[i], in_pitch[i], row, (size_t)height[i], cudaMemcpyHostToDevice,
+                      c->s_h2d));
+    HR_CUDA(cudaEventRecord(c->ev_in_ready[b], c->s_h2d));
+    // the plain pipeline on the caller's stream, once the input is in and the D2H of image i - 2
+    // has left output buffer b
+    HR_CUDA(cudaStreamWaitEvent(st, c->ev_in_ready[b], 0));
+    if (i >= 2) HR_CUDA(cudaStreamWaitEvent(st, c->ev_out_free[b], 0));
+    ImageDesc d{static_cast<const uint8_t*>(c->d_pp_in[b]), static_cast<uint8_t*>(c->d_pp_out[b]), width[i],
+                height[i], (long long)dpitch, (long long)dpitch};
+    hr_status s = run_pipeline(c, 1, &d, elem_bytes, st, false);
+    if (s != HR_OK) { cudaStreamSynchronize(c->s_h2d); cudaStreamSynchronize(c->s_d2h); return s; }
+    HR_CUDA(cudaEventRecord(c->ev_in_free[b], st));
+    HR_CUDA(cudaEventRecord(c->ev_done[b], st));
+    // D2H of image i
+    HR_CUDA(cudaStreamWaitEvent(c->s_d2h, c->ev_done[b], 0));
+    HR_CUDA(copy_rows(h_out[i], out_pitch[i], c->d_pp_out[b], dpitch, row, (size_t)height[i],
+                      cudaMemcpyDeviceToHost, c->s_d2h));
+    HR_CUDA(cudaEventRecord(c->ev_out_free[b], c->s_d2h));
+  }
+  HR_CUDA(cudaStreamSynchronize(c->s_h2d));
+  HR_CUDA(cudaStreamSynchronize(c->s_d2h));
   return histretinex_sync_status(c, stream);
 }
 
@@ -492,6 +578,16 @@ hr_status histretinex_destroy(hr_ctx* c) {
   cudaFreeHost(c->h_tile_start);
   cudaFree(c->d_io_in);
   cudaFree(c->d_io_out);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(c->d_pp_in[b]);
+    cudaFree(c->d_pp_out[b]);
+    if (c->ev_in_ready[b]) cudaEventDestroy(c->ev_in_ready[b]);
+    if (c->ev_in_free[b]) cudaEventDestroy(c->ev_in_free[b]);
+    if (c->ev_done[b]) cudaEventDestroy(c->ev_done[b]);
+    if (c->ev_out_free[b]) cudaEventDestroy(c->ev_out_free[b]);
+  }
+  if (c->s_h2d) cudaStreamDestroy(c->s_h2d);
+  if (c->s_d2h) cudaStreamDestroy(c->s_d2h);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->desc_done) cudaEventDestroy(c->desc_done);
   for (int i = 0; i < hr_ctx::kRing; ++i)

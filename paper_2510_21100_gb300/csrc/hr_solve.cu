@@ -364,9 +364,12 @@ __device__ void class_totals(const ClassPlan& P, const unsigned* csz, const unsi
     const unsigned len = pc.y & 0xffffu;
     const unsigned* cells = P.listp + pc.x;
     F acc = 0;
-    for (unsigned c = 0; c < len; ++c) {
-      const unsigned cell = cells[c];
-      acc = fmaF(Rc[cell >> 16], Lc[cell & 0xffffu], acc);
+#pragma unroll
+    for (unsigned c = 0; c < (unsigned)kPiece; ++c) {  // (all gathers of a piece in flight together)
+      if (c < len) {
+        const unsigned cell = cells[c];
+        acc = fmaF(Rc[cell >> 16], Lc[cell & 0xffffu], acc);
+      }
     }
     part[p - pbase] = acc;
   }
@@ -547,6 +550,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         F acc = 0.0;
         if (a < aB) {
           const int i = RI[a];
+#pragma unroll 4
           for (int b = gl; b < nL; b += GA) acc = fmaF(L2c[b], q[class_index(i, LJ[b], km1, inv_d)], acc);
         }
         for (int o = GA >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
@@ -584,6 +588,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         F acc = 0.0;
         if (b < bB) {
           const int j = LJ[b];
+#pragma unroll 4
           for (int a = gl; a < nR; a += GB) acc = fmaF(RRc[a], q[class_index(RI[a], j, km1, inv_d)], acc);
         }
         for (int o = GB >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);

@@ -162,3 +162,20 @@ def test_reserve_then_batches_up_to_the_reserved_size(hr):
         assert torch.equal(a, b)
     with pytest.raises(hrm.HistRetinexError):
         ctx.reserve(0)
+
+
+def test_host_sequence_equals_device_path(hr):
+    """histretinex_enhance_host_many: each host image gets exactly the device path's result."""
+    import torch
+    import paper_2510_21100_gb300 as hrm
+    ctx = hrm.Context(hrm.Params())
+    sizes = [(320, 240), (96, 64), (640, 360), (640, 360), (33, 17)]
+    imgs = [synth.low_light_image(w, h, seed=700 + i) for i, (w, h) in enumerate(sizes)]
+    hins = [torch.from_numpy(im).pin_memory() for im in imgs]
+    outs = ctx.enhance_host_many(hins)
+    ctx.check()
+    for im, o in zip(imgs, outs):
+        ref = ctx.enhance(torch.from_numpy(im).cuda()).cpu()
+        assert torch.equal(o, ref)
+    outs2 = ctx.enhance_host_many(hins[:1])  # a second call reuses the buffers
+    assert torch.equal(outs2[0], outs[0])
