@@ -173,9 +173,10 @@ hr_status ensure_desc(hr_ctx* c, int n) {
   c->d_imgs = nullptr; c->d_tile_start = nullptr; c->h_imgs = nullptr; c->h_tile_start = nullptr; c->cap_imgs = 0;
   c->last_imgs.clear();
   HR_CUDA(cudaMalloc(&c->d_imgs, sizeof(ImageDesc) * (size_t)n));
-  HR_CUDA(cudaMalloc(&c->d_tile_start, sizeof(int) * 2 * (size_t)(n + 1)));  // tile starts, then strip starts
+  // tile starts, strip starts, then the solve's image order
+  HR_CUDA(cudaMalloc(&c->d_tile_start, sizeof(int) * 3 * (size_t)(n + 1)));
   HR_CUDA(cudaMallocHost(&c->h_imgs, sizeof(ImageDesc) * (size_t)n));
-  HR_CUDA(cudaMallocHost(&c->h_tile_start, sizeof(int) * 2 * (size_t)(n + 1)));
+  HR_CUDA(cudaMallocHost(&c->h_tile_start, sizeof(int) * 3 * (size_t)(n + 1)));
   c->cap_imgs = n;
   return HR_OK;
 }
@@ -227,6 +228,7 @@ cudaError_t enqueue_stages(hr_ctx* c, int n, int total, int units, int elem_byte
   a.fixed_iters = (c->p.flags & HR_FLAG_FIXED_ITERS) ? 1 : 0;
   a.jstart1 = c->d_jstart1;
   a.slots = c->d_slots;
+  a.order = c->d_tile_start + 2 * (n + 1);
   a.slot_bytes = c->lay.bytes;
   a.lay = c->lay;
   a.status = c->d_status;
@@ -282,8 +284,15 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
     }
     c->h_tile_start[n] = t;
     c->h_tile_start[2 * n + 1] = u;
+    // the solve's CTAs take the images largest first (longest solves first: the last wave holds
+    // the shortest ones)
+    int* order = c->h_tile_start + 2 * (n + 1);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order, order + n, [&](int x, int y) {
+      return (long long)imgs[x].W * imgs[x].H > (long long)imgs[y].W * imgs[y].H;
+    });
     HR_CUDA(cudaMemcpyAsync(c->d_imgs, c->h_imgs, sizeof(ImageDesc) * (size_t)n, cudaMemcpyHostToDevice, st));
-    HR_CUDA(cudaMemcpyAsync(c->d_tile_start, c->h_tile_start, sizeof(int) * 2 * (size_t)(n + 1),
+    HR_CUDA(cudaMemcpyAsync(c->d_tile_start, c->h_tile_start, sizeof(int) * 3 * (size_t)(n + 1),
                             cudaMemcpyHostToDevice, st));
     HR_CUDA(cudaEventRecord(c->desc_done, st));
     c->last_imgs.assign(imgs, imgs + n);

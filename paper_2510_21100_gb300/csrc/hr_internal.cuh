@@ -69,6 +69,7 @@ struct SolveArgs {
   int fixed_iters;
   const uint16_t* jstart1;   // [K][K+1]: first illumination bin j with index_1(i, j) >= k
   uint8_t* slots;            // base of slot 0
+  const int* order;          // CTA group g solves image order[g] (nullptr: image g)
   size_t slot_bytes;
   SlotLayout lay;
   unsigned* status;

@@ -405,7 +405,8 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   const int K = A.K;
   const F alpha = (F)A.alpha, beta = (F)A.beta, eps = (F)A.eps;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint8_t* slot = A.slots + (size_t)(blockIdx.x / C) * A.slot_bytes;
+  const int image = A.order ? A.order[blockIdx.x / C] : (int)(blockIdx.x / C);
+  uint8_t* slot = A.slots + (size_t)image * A.slot_bytes;
   const SlotLayout& lay = A.lay;
   const unsigned* S = reinterpret_cast<const unsigned*>(slot + lay.S);
   const unsigned* G = reinterpret_cast<const unsigned*>(slot + lay.G);
