@@ -50,11 +50,12 @@ def workload_config(W, H):
             "image": f"{W}x{H}", "K": 256, "iterations": 10, "elem": "uint8", "l2": "rotating inputs > L2"}
 
 
-def make_images(W, H):
-    """The seeded synthetic image plus two mirrored copies (distinct buffers for L2 rotation)."""
+def make_images(W, H, rank=0):
+    """This rank's seeded synthetic image plus two mirrored copies (distinct buffers for L2 rotation);
+    every rank draws its own image (rank 0's is the single-GPU workload image)."""
     import numpy as np
-    from paper_2510_21100_gb300 import synth
-    img = synth.low_light_image(W, H, seed=synth.seed_for(1, 0))
+    from paper_2510_21100_gb300 import shard, synth
+    img = synth.low_light_image(W, H, seed=shard.rank_image_seeds(rank, 1)[0])
     return [img, np.ascontiguousarray(img[:, ::-1]), np.ascontiguousarray(img[::-1])]
 
 
@@ -318,7 +319,7 @@ def main():
         dist.barrier()
 
     W, H = a.width, a.height
-    imgs = make_images(W, H)
+    imgs = make_images(W, H, rank)
     dins = [torch.from_numpy(im).cuda() for im in imgs]
     douts = [torch.empty_like(d) for d in dins]
     ctx = hr.Context(hr.Params(stage_timing=True), device=local)
@@ -333,13 +334,10 @@ def main():
     ms_total, launches, stage = timed_loop(ctx, dins, douts, a.steps, a.warmup, dist, torch)
     clocks = sampler.result()
 
-    ms_step = ms_total / a.steps
-    if dist is not None:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    from paper_2510_21100_gb300 import shard
+    ms_step = shard.max_over_ranks(ms_total / a.steps, dist, device="cuda")
     mp = W * H / 1e6
-    value = world * mp / (ms_step / 1000.0)
+    value = shard.job_throughput(world, mp, ms_step)
 
     pk, pk_src = peaks()
     b = 1
