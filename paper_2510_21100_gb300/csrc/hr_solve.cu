@@ -117,14 +117,22 @@ __device__ __forceinline__ df64 rcpF(df64 d) {
   return df_norm(x, __fmul_rn(x, r));
 }
 
-// index(i, j) = floor((2 i j + K - 1) / (2 (K - 1))): nearest level to i j / (K - 1).
-// The quotient is < K <= 4096, so a float estimate is within one of it.
-__device__ __forceinline__ int class_index(int i, int j, int km1, float inv_d) {
-  const int n = 2 * i * j + km1, d = 2 * km1;
-  int q = __float2int_rz(__int2float_rn(n) * inv_d);
-  const int r = n - q * d;
-  q += (r < 0) ? -1 : (r >= d ? 1 : 0);
-  return q;
+// index(i, j) = floor((2 i j + K - 1) / (2 (K - 1))): nearest level to i j / (K - 1).  The divisor
+// d = 2 (K - 1) is fixed, so the quotient is a high multiply by M = ceil(2^(32+l) / d), l = floor(log2 d),
+// and a shift (Granlund and Montgomery, division by invariant integers using multiplication): with
+// e = M d - 2^(32+l) < d, n M / 2^(32+l) = n / d + n e / (d 2^(32+l)) stays below the next integer
+// while n e < 2^(32+l), and n < 2 K^2, e < 2 K bound n e by 4 K^3, far below 2^(32+l) >= 2^31 d.
+struct ClassDiv {
+  unsigned m;
+  int l;
+  __device__ explicit ClassDiv(int km1) {
+    const unsigned d = 2u * (unsigned)km1;
+    l = 31 - __clz(d);
+    m = (unsigned)(((1ull << (32 + l)) + d - 1) / d);  // < 2^32: d is not a power of two
+  }
+};
+__device__ __forceinline__ int class_index(int i, int j, int km1, const ClassDiv& cd) {
+  return (int)(__umulhi((unsigned)(2 * i * j + km1), cd.m) >> cd.l);
 }
 
 // First illumination bin j with index(i, j) >= k: ceil((2k-1)(K-1) / (2i)), at most K.
@@ -478,7 +486,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   const F invN = rcpF(N);
   const F invNN = rcpF(N * N);
   const int km1 = K - 1;
-  const float inv_d = 1.0f / (float)(2 * km1);
+  const ClassDiv cdiv(km1);
 
   // ---- Eq. 11 classes that matter (S_k > 0): plan and own cell lists -------------------------
   cl.sync();  // every CTA of the cluster has started before any distributed shared memory access
@@ -552,7 +560,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         if (a < aB) {
           const int i = RI[a];
 #pragma unroll 4
-          for (int b = gl; b < nL; b += GA) acc = fmaF(L2c[b], q[class_index(i, LJ[b], km1, inv_d)], acc);
+          for (int b = gl; b < nL; b += GA) acc = fmaF(L2c[b], q[class_index(i, LJ[b], km1, cdiv)], acc);
         }
         for (int o = GA >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
         if (gl == 0 && a < aB) {
@@ -590,7 +598,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         if (b < bB) {
           const int j = LJ[b];
 #pragma unroll 4
-          for (int a = gl; a < nR; a += GB) acc = fmaF(RRc[a], q[class_index(RI[a], j, km1, inv_d)], acc);
+          for (int a = gl; a < nR; a += GB) acc = fmaF(RRc[a], q[class_index(RI[a], j, km1, cdiv)], acc);
         }
         for (int o = GB >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
         if (gl == 0 && b < bB) Bs[b] = acc;
