@@ -423,8 +423,10 @@ def main():
         line["per_size"] = per
         line["batched"] = batched_leg(torch, hr, local, hr.PREC_DF64)
         line["batched_fp64"] = batched_leg(torch, hr, local, hr.PREC_FP64)
-        line["precision"] = precision_leg(torch, hr, local)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()  # the legs' device buffers go back before the latency-sensitive one
         line["serving"] = serving_leg(torch, hr, local, imgs[0])
+        line["precision"] = precision_leg(torch, hr, local)
         rate, reps, shape = cpu_oracle_rate(imgs, seconds=10.0)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{reps} x full {shape[1]}x{shape[0]} image, single-threaded FP64 C oracle"}
