@@ -504,9 +504,27 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   // own rows and columns of the updates (contiguous slices)
   const int aA = (int)((long long)nR * rank / C), aB = (int)((long long)nR * (rank + 1) / C);
   const int bA = (int)((long long)nL * rank / C), bB = (int)((long long)nL * (rank + 1) / C);
-  const int GA = C == 1 ? 4 : 16;   // lanes per row in the Eq. 13 sums
-  const int GB = C == 1 ? 4 : 32;   // lanes per column in the Eq. 12 sums
-  // (one image's arithmetic depends on C only through these group sizes and the class split)
+  // Lanes per row in the Eq. 13 sums (GA) and per column in the Eq. 12 sums (GB).  A warp-wide FP64
+  // instruction holds its SM sub-partition's FP64 pipe for about 64 cycles however many lanes are
+  // active, while one lane's sum is a chain of dependent steps, so for a cluster CTA the choice
+  // minimises the larger of the busiest sub-partition's FP64 cycles, ceil(warps / 4) x (terms per
+  // lane + shuffle-tree levels) x 64, and a lane's chain.  A CTA alone (batches: one image per CTA,
+  // many rows each) uses 4.  (One image's arithmetic depends on C only
+  // through these group sizes and the class split.)
+  auto group = [&](int own, int terms) {
+    if (C == 1) return 4;
+    int best = 32, cost = 1 << 30;
+    for (int g = 4, lg = 2; g <= 32; g <<= 1, ++lg) {
+      const int warps = (own * g + 31) / 32, t = (terms + g - 1) / g;
+      const int pipe = ((warps + 3) / 4) * (t + lg) * 64;  // cycles of the busiest FP64 pipe
+      const int chain = t * 110 + lg * 100;               // one lane's dependent steps
+      const int c = pipe > chain ? pipe : chain;
+      if (c < cost) { cost = c; best = g; }
+    }
+    return best;
+  };
+  const int GA = group(aB - aA, nL);
+  const int GB = group(bB - bA, nR);
 
   for (int a = tid; a < nR; a += NT) Rc[a] = (F)G[RI[a]];   // R^(0) = H_C(grad S)
   for (int b = tid; b < nL; b += NT) Lc[b] = (F)S[LJ[b]];   // L^(0) = H_C(S)
@@ -533,15 +551,17 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         const F sl = it == 0 ? 1.0 : N * rcpF(s1);
         scal[3] = sl;
         scal[0] = rcpF(fmaF(s2 * (sl * sl), invNN, beta));
-      }
+      }  // (the second reciprocal needs the first: a chain)
     }
     for (int b = tid; b < nL; b += NT) { const F x = L0[b]; L2c[b] = x * x; }
     if (it == 1) stamp();
-    class_totals<F>(PP, csz, pst, R0, L0, [&](int c, F Pu) {  // (after a barrier: scal[3] is set)
+    class_totals<F>(PP, csz, pst, R0, L0, [&](int c, F Pu) { RRc[c] = Pu; });  // (R'R is free until Eq. 13)
+    __syncthreads();
+    for (int c = PP.cA + tid; c < PP.cB; c += NT) {  // q of all own classes together (scal[3] is set)
       const int k = LJ[c];
-      const F P = Pu * (scR * scal[3]);
+      const F P = RRc[c] * (scR * scal[3]);
       q[k] = P > 0.0 ? Sd[k] * rcpF(P) : 0.0;
-    });
+    }
     __syncthreads();
     if (it == 1) stamp();
     cl.sync();
@@ -587,7 +607,11 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         s1 += __shfl_xor_sync(FULL, s1, o);
         s2 += __shfl_xor_sync(FULL, s2, o);
       }
-      if (lane == 0) { scal[1] = rcpF(fmaF(s2, invNN, alpha)); scal[2] = N * rcpF(s1); }
+      // the two reciprocals side by side in lanes 0 and 1 (one instruction stream)
+      const F den = lane == 0 ? fmaF(s2, invNN, alpha) : s1;
+      const F rd = rcpF(den);
+      if (lane == 0) scal[1] = rd;
+      if (lane == 1) scal[2] = N * rd;
     }
     {
       F* Bs = L2c;  // column sums (L^2 is not needed again in this iteration)
