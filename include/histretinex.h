@@ -93,12 +93,17 @@ typedef struct hr_ctx hr_ctx;
  * default 16, lowered automatically when that cluster cannot be resident); use_graph: 1 to
  * capture enhance_batch's launches into a CUDA graph that is replayed while the batch's geometry
  * (image count, sizes, element size, alignment) is unchanged (default 1).  Stage timing is not
- * recorded for graph replays. */
+ * recorded for graph replays.  pdl: which kernels are programmatic dependent launches (bit 0 the
+ * histogram pass, bit 1 the solve, bit 2 the apply pass; 0..7): such a kernel is scheduled while
+ * the kernel before it on the stream finishes and waits on the device for that kernel's results
+ * (default 5, the two pixel passes; 0: plain stream order).  A dependent solve measured slower on
+ * GB300 (its cluster is placed while the histogram pass drains). */
 typedef struct {
   int hist_ctas_per_sm;
   int apply_ctas_per_sm;
   int solve_cluster;
   int use_graph;
+  int pdl;
 } hr_tuning;
 
 /* Fills *p with the defaults: K = 256, alpha = beta = 1e-3, gamma = 2.2 (Sec. III.C),

@@ -48,6 +48,7 @@ class hr_tuning(ctypes.Structure):
         ("apply_ctas_per_sm", ctypes.c_int),
         ("solve_cluster", ctypes.c_int),
         ("use_graph", ctypes.c_int),
+        ("pdl", ctypes.c_int),
     ]
 
 

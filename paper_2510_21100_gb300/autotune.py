@@ -1,7 +1,7 @@
 """Launch-shape autotuner for the HistRetinex pipeline.
 
 Times candidate launch shapes (CTAs per SM of the two pixel passes, cluster size of a single
-image's solve) on the caller's own images with CUDA events, keeps the fastest, applies it to the
+image's solve, which kernels are programmatic dependent launches) on the caller's own images with CUDA events, keeps the fastest, applies it to the
 context and caches it in a JSON file keyed by GPU, K, element size, batch-size bucket and
 image-size bucket.  Coordinate descent: one field at a time, the others held at their best.
 """
@@ -17,6 +17,7 @@ CANDIDATES = {
     "hist_ctas_per_sm": (2, 4, 8),
     "apply_ctas_per_sm": (4, 8, 16),
     "solve_cluster": (4, 8, 16),
+    "pdl": (0, 1, 5),  # dependent launches: none, histogram pass, histogram and apply passes
 }
 
 
@@ -60,7 +61,7 @@ def autotune(ctx, ins, outs=None, reps: int = 5, cache_path: str | None = DEFAUL
         return cache[key]["tuning"], cache[key]["ms"]
     best = ctx.tuning()
     best_ms = _time(ctx, ins, outs, reps, torch)
-    fields = ["hist_ctas_per_sm", "apply_ctas_per_sm"] + (["solve_cluster"] if len(ins) == 1 else [])
+    fields = ["hist_ctas_per_sm", "apply_ctas_per_sm"] + (["solve_cluster"] if len(ins) == 1 else []) + ["pdl"]
     for field in fields:
         for v in CANDIDATES[field]:
             if v == best[field]:

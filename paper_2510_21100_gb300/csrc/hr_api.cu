@@ -11,6 +11,7 @@
 
 using hr::ImageDesc;
 using hr::SlotLayout;
+using hr::ImgTab;
 
 struct hr_ctx {
   int device = 0;
@@ -46,11 +47,14 @@ struct hr_ctx {
   int ev_next = 0;
   double stage_ms[3] = {0, 0, 0};
   int stage_calls = 0;
-  hr_tuning tune{8, 8, 16, 1};
+  hr_tuning tune{8, 8, 16, 1, 5};
+  // leading slots whose H_C(S) and H_C(grad S) are known to be zero (the solve clears them after
+  // use unless the intermediates are kept for histretinex_get_debug)
+  int hist_clean = 0;
   // captured batch pipeline and the geometry it was captured for
   cudaGraphExec_t graph = nullptr;
-  int g_n = 0, g_total = 0, g_eb = 0, g_fast_in = 0, g_fast_out = 0;
-  hr_tuning g_tune{0, 0, 0, 0};
+  int g_n = 0, g_total = 0, g_eb = 0, g_fast_in = 0, g_fast_out = 0, g_zero = 0;
+  hr_tuning g_tune{0, 0, 0, 0, 0};
 };
 
 namespace hr {
@@ -160,6 +164,7 @@ hr_status ensure_slots(hr_ctx* c, int n) {
   if (n <= c->n_slots) return HR_OK;
   drop_graph(c);
   if (c->d_slots) { cudaFree(c->d_slots); c->d_slots = nullptr; c->n_slots = 0; }
+  c->hist_clean = 0;
   HR_CUDA(cudaMalloc(&c->d_slots, c->lay.bytes * (size_t)n));
   c->n_slots = n;
   return HR_OK;
@@ -204,19 +209,23 @@ hr_status fold_timing(hr_ctx* c, int i) {
   return HR_OK;
 }
 
-// The pipeline's device work on one stream: zero the histograms, histogram pass, solve, apply.
-// ev (optional): four events recorded around the three stages.
-cudaError_t enqueue_stages(hr_ctx* c, int n, int total, int units, int elem_bytes, bool fast_in, bool fast_out,
-                           bool batched, cudaStream_t st, cudaEvent_t* ev) {
-  const int K = c->p.K;
+// The pipeline's device work on one stream: zero the histograms (unless the previous solves left
+// them zero), histogram pass, solve, apply.  ev (optional): four events recorded around the three
+// stages.
+cudaError_t enqueue_stages(hr_ctx* c, const ImgTab& tab, int total, int units, int elem_bytes, bool fast_in,
+                           bool fast_out, bool batched, bool zero, cudaStream_t st, cudaEvent_t* ev) {
+  const int K = c->p.K, n = tab.n;
+  const int pdl = c->tune.pdl;  // bit 0: histogram pass, bit 1: solve, bit 2: apply pass
+  const bool debug = (c->p.flags & HR_FLAG_DEBUG_OUT) != 0;
   cudaError_t e;
   // zero H_C(S) and H_C(grad S) of every slot used (S and G are adjacent at the slot start)
-  e = cudaMemset2DAsync(c->d_slots + c->lay.S, c->lay.bytes, 0, (size_t)2 * K * sizeof(unsigned), (size_t)n, st);
-  if (e != cudaSuccess) return e;
+  if (zero) {
+    e = cudaMemset2DAsync(c->d_slots + c->lay.S, c->lay.bytes, 0, (size_t)2 * K * sizeof(unsigned), (size_t)n, st);
+    if (e != cudaSuccess) return e;
+  }
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-  e = hr::launch_hist(c->d_imgs, n, c->d_tile_start, total, c->d_tile_start + n + 1, units, elem_bytes, K,
-                      c->d_slots, c->lay.bytes, c->lay, c->d_status, c->sm_count, c->tune.hist_ctas_per_sm, st,
-                      fast_in);
+  e = hr::launch_hist(tab, total, units, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay, c->d_status, c->sm_count,
+                      c->tune.hist_ctas_per_sm, st, fast_in, (pdl & 1) != 0);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
   hr::SolveArgs a{};
@@ -228,20 +237,28 @@ cudaError_t enqueue_stages(hr_ctx* c, int n, int total, int units, int elem_byte
   a.fixed_iters = (c->p.flags & HR_FLAG_FIXED_ITERS) ? 1 : 0;
   a.jstart1 = c->d_jstart1;
   a.slots = c->d_slots;
-  a.order = c->d_tile_start + 2 * (n + 1);
+  a.order = n > 1 ? c->d_tile_start + 2 * (n + 1) : nullptr;
   a.slot_bytes = c->lay.bytes;
   a.lay = c->lay;
   a.status = c->d_status;
-  a.profile = (c->p.flags & HR_FLAG_DEBUG_OUT) ? 1 : 0;
+  a.profile = debug ? 1 : 0;
+  a.zero_hist = debug ? 0 : 1;
   a.arith = c->p.precision == HR_PREC_FP32 ? hr::kArithF32 : (c->p.precision == HR_PREC_DF64 ? hr::kArithDF64 : hr::kArithF64);
-  e = hr::launch_solve(a, n, batched ? 1 : c->tune.solve_cluster, st);
+  e = hr::launch_solve(a, n, batched ? 1 : c->tune.solve_cluster, st, (pdl & 2) != 0);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
-  e = hr::launch_apply(c->d_imgs, n, c->d_tile_start, total, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay,
-                       c->d_status, c->sm_count * c->tune.apply_ctas_per_sm, st, fast_out);
+  e = hr::launch_apply(tab, total, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay, c->d_status,
+                       c->sm_count * c->tune.apply_ctas_per_sm, st, fast_out, (pdl & 4) != 0);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return e;
   return cudaSuccess;
+}
+
+// Slots [0, n) after a call that enqueued its stages (ok) or failed to: the solve clears the
+// histograms it used unless debug intermediates are kept.
+void note_hist_state(hr_ctx* c, int n, bool ok) {
+  if (!ok || (c->p.flags & HR_FLAG_DEBUG_OUT)) c->hist_clean = 0;
+  else if (n > c->hist_clean) c->hist_clean = n;
 }
 
 hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, cudaStream_t st, bool batched) {
@@ -270,38 +287,56 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
   }
   hr_status s = ensure_slots(c, n);
   if (s != HR_OK) return s;
-  s = ensure_desc(c, n);
-  if (s != HR_OK) return s;
-  if (!same_desc(c->last_imgs, imgs, n)) {
-    HR_CUDA(cudaEventSynchronize(c->desc_done));  // the previous upload has left the staging buffer
-    int t = 0, u = 0;
-    for (int i = 0; i < n; ++i) {
-      c->h_imgs[i] = imgs[i];
-      c->h_tile_start[i] = t;
-      c->h_tile_start[n + 1 + i] = u;
-      t += hr::tiles_of(imgs[i].W, imgs[i].H);
-      u += hr::strips_of(imgs[i].W, imgs[i].H);
+  ImgTab tab{};
+  tab.n = n;
+  if (n == 1) {
+    tab.one = imgs[0];  // travels in the kernel parameters: nothing to upload
+  } else {
+    s = ensure_desc(c, n);
+    if (s != HR_OK) return s;
+    if (!same_desc(c->last_imgs, imgs, n)) {
+      HR_CUDA(cudaEventSynchronize(c->desc_done));  // the previous upload has left the staging buffer
+      int t = 0, u = 0;
+      for (int i = 0; i < n; ++i) {
+        c->h_imgs[i] = imgs[i];
+        c->h_tile_start[i] = t;
+        c->h_tile_start[n + 1 + i] = u;
+        t += hr::tiles_of(imgs[i].W, imgs[i].H);
+        u += hr::strips_of(imgs[i].W, imgs[i].H);
+      }
+      c->h_tile_start[n] = t;
+      c->h_tile_start[2 * n + 1] = u;
+      // the solve's CTAs take the images largest first (longest solves first: the last wave holds
+      // the shortest ones)
+      int* order = c->h_tile_start + 2 * (n + 1);
+      for (int i = 0; i < n; ++i) order[i] = i;
+      std::stable_sort(order, order + n, [&](int x, int y) {
+        return (long long)imgs[x].W * imgs[x].H > (long long)imgs[y].W * imgs[y].H;
+      });
+      HR_CUDA(cudaMemcpyAsync(c->d_imgs, c->h_imgs, sizeof(ImageDesc) * (size_t)n, cudaMemcpyHostToDevice, st));
+      HR_CUDA(cudaMemcpyAsync(c->d_tile_start, c->h_tile_start, sizeof(int) * 3 * (size_t)(n + 1),
+                              cudaMemcpyHostToDevice, st));
+      HR_CUDA(cudaEventRecord(c->desc_done, st));
+      c->last_imgs.assign(imgs, imgs + n);
     }
-    c->h_tile_start[n] = t;
-    c->h_tile_start[2 * n + 1] = u;
-    // the solve's CTAs take the images largest first (longest solves first: the last wave holds
-    // the shortest ones)
-    int* order = c->h_tile_start + 2 * (n + 1);
-    for (int i = 0; i < n; ++i) order[i] = i;
-    std::stable_sort(order, order + n, [&](int x, int y) {
-      return (long long)imgs[x].W * imgs[x].H > (long long)imgs[y].W * imgs[y].H;
-    });
-    HR_CUDA(cudaMemcpyAsync(c->d_imgs, c->h_imgs, sizeof(ImageDesc) * (size_t)n, cudaMemcpyHostToDevice, st));
-    HR_CUDA(cudaMemcpyAsync(c->d_tile_start, c->h_tile_start, sizeof(int) * 3 * (size_t)(n + 1),
-                            cudaMemcpyHostToDevice, st));
-    HR_CUDA(cudaEventRecord(c->desc_done, st));
-    c->last_imgs.assign(imgs, imgs + n);
+    tab.imgs = c->d_imgs;
+    tab.tiles = c->d_tile_start;
+    tab.units = c->d_tile_start + n + 1;
   }
+  const bool debug = (c->p.flags & HR_FLAG_DEBUG_OUT) != 0;
   const bool timing = (c->p.flags & HR_FLAG_STAGE_TIMING) != 0;
   const bool graph = batched && c->tune.use_graph && n > 1 && !timing;
   if (graph) {
+    // a replayed graph cannot see whether the histograms are zero: without debug intermediates it
+    // relies on the solves clearing them (cleared here first if need be), with them it zeroes
+    if (!debug && c->hist_clean < n) {
+      cudaError_t e = cudaMemset2DAsync(c->d_slots + c->lay.S, c->lay.bytes, 0, (size_t)2 * c->p.K * sizeof(unsigned),
+                                        (size_t)n, st);
+      if (e != cudaSuccess) { note_hist_state(c, n, false); return cuda_fail(e); }
+      c->hist_clean = n;
+    }
     const bool same = c->graph && c->g_n == n && c->g_total == (int)total && c->g_eb == elem_bytes &&
-                      c->g_fast_in == (int)fast_in && c->g_fast_out == (int)fast_out &&
+                      c->g_fast_in == (int)fast_in && c->g_fast_out == (int)fast_out && c->g_zero == (int)debug &&
                       std::memcmp(&c->g_tune, &c->tune, sizeof(hr_tuning)) == 0;
     if (!same) {
       drop_graph(c);
@@ -310,7 +345,7 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        e = enqueue_stages(c, n, (int)total, (int)units, elem_bytes, fast_in, fast_out, batched, cap, nullptr);
+        e = enqueue_stages(c, tab, (int)total, (int)units, elem_bytes, fast_in, fast_out, batched, debug, cap, nullptr);
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         if (e == cudaSuccess) e = e2;
       }
@@ -319,9 +354,11 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
       cudaStreamDestroy(cap);
       if (e != cudaSuccess) { c->graph = nullptr; return cuda_fail(e); }
       c->g_n = n; c->g_total = (int)total; c->g_eb = elem_bytes;
-      c->g_fast_in = (int)fast_in; c->g_fast_out = (int)fast_out; c->g_tune = c->tune;
+      c->g_fast_in = (int)fast_in; c->g_fast_out = (int)fast_out; c->g_zero = (int)debug; c->g_tune = c->tune;
     }
-    HR_CUDA(cudaGraphLaunch(c->graph, st));
+    const cudaError_t e = cudaGraphLaunch(c->graph, st);
+    note_hist_state(c, n, e == cudaSuccess);
+    if (e != cudaSuccess) return cuda_fail(e);
     c->launches += 3;
     c->last_n = n;
     return HR_OK;
@@ -337,7 +374,10 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
     ev = c->ev[i];
     c->ev_used[i] = true;
   }
-  HR_CUDA(enqueue_stages(c, n, (int)total, (int)units, elem_bytes, fast_in, fast_out, batched, st, ev));
+  const bool zero = debug || c->hist_clean < n;
+  const cudaError_t e = enqueue_stages(c, tab, (int)total, (int)units, elem_bytes, fast_in, fast_out, batched, zero, st, ev);
+  note_hist_state(c, n, e == cudaSuccess);
+  if (e != cudaSuccess) return cuda_fail(e);
   c->launches += 3;
   c->last_n = n;
   return HR_OK;
@@ -636,6 +676,7 @@ hr_status histretinex_set_tuning(hr_ctx* c, const hr_tuning* t) {
   if (t->solve_cluster < 1 || t->solve_cluster > 16 || (t->solve_cluster & (t->solve_cluster - 1)))
     return HR_ERR_INVALID_ARG;
   if (t->use_graph != 0 && t->use_graph != 1) return HR_ERR_INVALID_ARG;
+  if (t->pdl < 0 || t->pdl > 7) return HR_ERR_INVALID_ARG;
   c->tune = *t;
   return HR_OK;
 }

@@ -31,6 +31,46 @@ struct ImageDesc {
   long long in_pitch, out_pitch;
 };
 
+// The images of a launch.  One image travels inline in the kernel parameters, so a single-image
+// call uploads nothing before its kernels; several are read from device tables.
+struct ImgTab {
+  const ImageDesc* imgs;   // n descriptors (n > 1)
+  const int* tiles;        // n + 1 tile starts (n > 1)
+  const int* units;        // n + 1 strip starts (n > 1)
+  int n;
+  ImageDesc one;           // the image (n == 1)
+#ifdef __CUDACC__
+  __device__ __forceinline__ ImageDesc desc(int i) const { return n == 1 ? one : imgs[i]; }
+  __device__ __forceinline__ int tile0(int i) const { return n == 1 ? 0 : __ldg(tiles + i); }
+  __device__ __forceinline__ int unit0(int i) const { return n == 1 ? 0 : __ldg(units + i); }
+#endif
+};
+
+#ifdef __CUDACC__
+// Programmatic dependent launch, device side: wait until the previous kernel on the stream has
+// finished and its writes are visible (returns at once for a plain launch), and let the next
+// kernel be scheduled (it waits in turn for this one to finish).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Kernel launch with the programmatic-stream-serialisation attribute when pdl is set.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
+                          Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<Args&&>(args)...);
+}
+#endif
+
 // Byte offsets of the per-image workspace ("slot").  Every slot has the same layout for a
 // given K; slots are `slot_bytes` apart.
 struct SlotLayout {
@@ -77,20 +117,22 @@ struct SolveArgs {
   int list_in_smem;          // 1: own cell lists may use shared memory (set by launch_solve)
   int profile;               // 1: record phase timestamps into the slot's misc area
   int arith;                 // kArithF64 (plain form), kArithF32 (reduced precision), kArithDF64
+  int zero_hist;             // 1: clear H_C(S) and H_C(grad S) after use, ready for the next call
 };
 
-// Launchers (return cudaError_t of the launch).
+// Launchers (return cudaError_t of the launch).  pdl: programmatic dependent launch (the kernel
+// may be scheduled before the previous kernel on the stream has finished; it waits for it on the
+// device before touching any data).
 // The histogram pass walks the tile list or, for one large 8-bit image with aligned rows, the
 // strip list (kStripW x kBandH units); both lists are given, with their totals.  Tile kernels
 // run sms x ctas_per_sm CTAs, the strip kernel one CTA per SM.
-cudaError_t launch_hist(const ImageDesc* d_imgs, int n, const int* d_tile_start, int total_tiles,
-                        const int* d_unit_start, int total_units, int elem_bytes, int K, uint8_t* slots,
+cudaError_t launch_hist(const ImgTab& tab, int total_tiles, int total_units, int elem_bytes, int K, uint8_t* slots,
                         size_t slot_bytes, SlotLayout lay, unsigned* status, int sms, int ctas_per_sm,
-                        cudaStream_t st, bool fast);
-cudaError_t launch_solve(const SolveArgs& a, int n, int cluster, cudaStream_t st);
-cudaError_t launch_apply(const ImageDesc* d_imgs, int n, const int* d_tile_start, int total_tiles, int elem_bytes,
+                        cudaStream_t st, bool fast, bool pdl);
+cudaError_t launch_solve(const SolveArgs& a, int n, int cluster, cudaStream_t st, bool pdl);
+cudaError_t launch_apply(const ImgTab& tab, int total_tiles, int elem_bytes,
                          int K, uint8_t* slots, size_t slot_bytes, SlotLayout lay, unsigned* status, int grid,
-                         cudaStream_t st, bool fast);
+                         cudaStream_t st, bool fast, bool pdl);
 size_t solve_smem_bytes(int K, int vec_in_smem, int list_in_smem, size_t fsize);
 
 // Geometry of the pixel passes: tiles of kTileW x kTileH pixels.

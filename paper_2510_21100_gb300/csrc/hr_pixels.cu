@@ -44,10 +44,13 @@ __device__ __forceinline__ unsigned round_sqrt(unsigned m2) {
 }
 
 template <typename ET>
-__global__ void __launch_bounds__(kThreads) hist_kernel(const ImageDesc* __restrict__ imgs, int n,
-                                                        const int* __restrict__ tile_start, int total, int K,
+__global__ void __launch_bounds__(kThreads) hist_kernel(const ImgTab tab, int total, int K,
                                                         uint8_t* slots, size_t slot_bytes, SlotLayout lay,
                                                         unsigned* status) {
+  pdl_wait();     // the previous kernel on the stream has finished
+  pdl_trigger();  // the next one may be scheduled (it waits for this one)
+  const int n = tab.n;
+  const int* __restrict__ tile_start = tab.tiles;  // (n > 1 only)
   extern __shared__ __align__(16) unsigned char smem[];
   // per-warp sub-histograms when K is small (less same-address contention), else one copy
   const int copies = K <= 256 ? kWarps : 1;
@@ -81,8 +84,8 @@ __global__ void __launch_bounds__(kThreads) hist_kernel(const ImageDesc* __restr
       }
       cur = img;
     }
-    const ImageDesc im = imgs[img];
-    const int lt = t - __ldg(tile_start + img);
+    const ImageDesc im = tab.desc(img);
+    const int lt = t - tab.tile0(img);
     const int tiles_x = (im.W + kTileW - 1) / kTileW;
     const int x0 = (lt % tiles_x) * kTileW, y0 = (lt / tiles_x) * kTileH;
     // V tile with a one-pixel halo; coordinates outside the image replicate the border
@@ -125,10 +128,13 @@ __global__ void __launch_bounds__(kThreads) hist_kernel(const ImageDesc* __restr
 }
 
 template <typename ET>
-__global__ void __launch_bounds__(kThreads) apply_kernel(const ImageDesc* __restrict__ imgs, int n,
-                                                         const int* __restrict__ tile_start, int total, int K,
+__global__ void __launch_bounds__(kThreads) apply_kernel(const ImgTab tab, int total, int K,
                                                          const uint8_t* slots, size_t slot_bytes, SlotLayout lay,
                                                          unsigned* status) {
+  pdl_wait();     // the previous kernel on the stream has finished
+  pdl_trigger();  // the next one may be scheduled (it waits for this one)
+  const int n = tab.n;
+  const int* __restrict__ tile_start = tab.tiles;  // (n > 1 only)
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned short* lut = reinterpret_cast<unsigned short*>(smem);
   float* rup = reinterpret_cast<float*>(smem + ((K * 2 + 15) & ~15));  // V'/V rounded up (8-bit data)
@@ -150,8 +156,8 @@ __global__ void __launch_bounds__(kThreads) apply_kernel(const ImageDesc* __rest
       __syncthreads();
       cur = img;
     }
-    const ImageDesc im = imgs[img];
-    const int lt = t - __ldg(tile_start + img);
+    const ImageDesc im = tab.desc(img);
+    const int lt = t - tab.tile0(img);
     const int tiles_x = (im.W + kTileW - 1) / kTileW;
     const int x0 = (lt % tiles_x) * kTileW, y0 = (lt / tiles_x) * kTileH;
     for (int e = tid; e < kTileH * kTileW; e += kThreads) {
@@ -459,10 +465,13 @@ __device__ __noinline__ bool hist_tile_edge(const LaneTile g, int yb, int mclip,
 }
 
 template <bool kClamp>
-__global__ void __launch_bounds__(kHT, 1) hist_u8r_kernel(const ImageDesc* __restrict__ imgs, int n,
-                                                         const int* __restrict__ unit_start, int total, int K,
+__global__ void __launch_bounds__(kHT, 1) hist_u8r_kernel(const ImgTab tab, int total, int K,
                                                          uint8_t* slots, size_t slot_bytes, SlotLayout lay,
                                                          unsigned* status) {
+  pdl_wait();     // the previous kernel on the stream has finished
+  pdl_trigger();  // the next one may be scheduled (it waits for this one)
+  const int n = tab.n;
+  const int* __restrict__ unit_start = tab.units;  // (n > 1 only)
   extern __shared__ __align__(16) unsigned char hsmem[];
   // per warp two copies (even and odd lanes, which see the most alike levels) of H_C(S), H_C(grad S)
   auto hist = reinterpret_cast<unsigned (*)[2][2][kHBins]>(hsmem);
@@ -510,12 +519,12 @@ __global__ void __launch_bounds__(kHT, 1) hist_u8r_kernel(const ImageDesc* __res
       if (cur >= 0) flush_warp(cur);
       cur = img;
     }
-    const ImageDesc& im = imgs[img];
+    const ImageDesc im = tab.desc(img);
     g.in = im.in;
     g.pitch = im.in_pitch;
     g.W = im.W;
     g.H = im.H;
-    const int lt = t - __ldg(unit_start + img);
+    const int lt = t - tab.unit0(img);
     const int strips_x = (g.W + kStripW - 1) / kStripW;
     g.x0 = (lt % strips_x) * kStripW;
     const int y0 = (lt / strips_x) * kBandH;
@@ -593,10 +602,13 @@ __device__ __forceinline__ unsigned grad_level(int m2, int K) {
 
 __device__ __forceinline__ unsigned byte_of(const unsigned (&w)[4], int k) { return (w[k >> 2] >> (8 * (k & 3))) & 0xffu; }
 
-__global__ void __launch_bounds__(kThreads) hist_u8v_kernel(const ImageDesc* __restrict__ imgs, int n,
-                                                            const int* __restrict__ tile_start, int total, int K,
+__global__ void __launch_bounds__(kThreads) hist_u8v_kernel(const ImgTab tab, int total, int K,
                                                             uint8_t* slots, size_t slot_bytes, SlotLayout lay,
                                                             unsigned* status) {
+  pdl_wait();     // the previous kernel on the stream has finished
+  pdl_trigger();  // the next one may be scheduled (it waits for this one)
+  const int n = tab.n;
+  const int* __restrict__ tile_start = tab.tiles;  // (n > 1 only)
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned* hs = reinterpret_cast<unsigned*>(smem);        // per-warp H_C(S) copies
   unsigned* hg = hs + kWarps * K;                          // per-warp H_C(grad S) copies
@@ -614,8 +626,8 @@ __global__ void __launch_bounds__(kThreads) hist_u8v_kernel(const ImageDesc* __r
   bool range_bad = false;
   auto tile_xy = [&](int t, int& img, int& x0, int& y0) {
     img = image_of_tile(tile_start, n, t);
-    const ImageDesc& im = imgs[img];
-    const int lt = t - __ldg(tile_start + img);
+    const ImageDesc im = tab.desc(img);
+    const int lt = t - tab.tile0(img);
     const int tiles_x = (im.W + kTileW - 1) / kTileW;
     x0 = (lt % tiles_x) * kTileW;
     y0 = (lt / tiles_x) * kTileH;
@@ -639,7 +651,7 @@ __global__ void __launch_bounds__(kThreads) hist_u8v_kernel(const ImageDesc* __r
   if (t0 < t1) {
     int img, x0, y0;
     tile_xy(t0, img, x0, y0);
-    stage_tile(imgs[img], x0, y0, raw);
+    stage_tile(tab.desc(img), x0, y0, raw);
   }
   for (int t = t0; t < t1; ++t) {
     int img, x0, y0;
@@ -648,7 +660,7 @@ __global__ void __launch_bounds__(kThreads) hist_u8v_kernel(const ImageDesc* __r
     if (t + 1 < t1) {
       int img2, x2, y2;
       tile_xy(t + 1, img2, x2, y2);
-      stage_tile(imgs[img2], x2, y2, raw + ((t + 1 - t0) & 1) * (kVH * kRawRow));
+      stage_tile(tab.desc(img2), x2, y2, raw + ((t + 1 - t0) & 1) * (kVH * kRawRow));
     } else {
       cp_async_commit();
     }
@@ -658,7 +670,7 @@ __global__ void __launch_bounds__(kThreads) hist_u8v_kernel(const ImageDesc* __r
       if (cur >= 0) flush(cur);
       cur = img;
     }
-    const ImageDesc im = imgs[img];
+    const ImageDesc im = tab.desc(img);
     // V = max(r, g, b), four pixels per thread: staged bytes 12u+4 .. 12u+15 hold columns 4u .. 4u+3
     for (int e = tid; e < kVH * kVGroups; e += kThreads) {
       const int r = e / kVGroups, u = e - r * kVGroups;
@@ -727,10 +739,13 @@ __global__ void __launch_bounds__(kThreads) hist_u8v_kernel(const ImageDesc* __r
   if (range_bad) atomicOr(status, kStRange);
 }
 
-__global__ void __launch_bounds__(kThreads) apply_u8v_kernel(const ImageDesc* __restrict__ imgs, int n,
-                                                             const int* __restrict__ tile_start, int total, int K,
+__global__ void __launch_bounds__(kThreads) apply_u8v_kernel(const ImgTab tab, int total, int K,
                                                              const uint8_t* slots, size_t slot_bytes, SlotLayout lay,
                                                              unsigned* status) {
+  pdl_wait();     // the previous kernel on the stream has finished
+  pdl_trigger();  // the next one may be scheduled (it waits for this one)
+  const int n = tab.n;
+  const int* __restrict__ tile_start = tab.tiles;  // (n > 1 only)
   // per level V: out_c = (c F_V + B_V) >> 18 with F_V = ceil(V' 2^18 / V), B_V = 2^17, which is
   // floor(c V'/V + 1/2) exactly for c <= V < 256 (the product is at most V' 2^18 + V < 2^32 and
   // overshoots by at most c / 2^18 < 1/(2V)); V = 0 gives F = 0, B = V' << 18.
@@ -753,8 +768,8 @@ __global__ void __launch_bounds__(kThreads) apply_u8v_kernel(const ImageDesc* __
       __syncthreads();
       cur = img;
     }
-    const ImageDesc im = imgs[img];
-    const int lt = t - __ldg(tile_start + img);
+    const ImageDesc im = tab.desc(img);
+    const int lt = t - tab.tile0(img);
     const int tiles_x = (im.W + kTileW - 1) / kTileW;
     const int x = (lt % tiles_x) * kTileW + 16 * (tid & 7);
     const int y = (lt / tiles_x) * kTileH + (tid >> 3);
@@ -800,26 +815,23 @@ __global__ void __launch_bounds__(kThreads) apply_u8v_kernel(const ImageDesc* __
 
 }  // namespace
 
-cudaError_t launch_hist(const ImageDesc* d_imgs, int n, const int* d_tile_start, int total_tiles,
-                        const int* d_unit_start, int total_units, int elem_bytes, int K, uint8_t* slots,
+cudaError_t launch_hist(const ImgTab& tab, int total_tiles, int total_units, int elem_bytes, int K, uint8_t* slots,
                         size_t slot_bytes, SlotLayout lay, unsigned* status, int sms, int ctas_per_sm,
-                        cudaStream_t st, bool fast) {
+                        cudaStream_t st, bool fast, bool pdl) {
   const int copies = K <= 256 ? kWarps : 1;
   const size_t smem = (size_t)2 * copies * K * sizeof(unsigned) + (size_t)kVH * kVW * sizeof(unsigned short);
   // strips for one large image (at least HR_STRIP_MIN_FACTOR per warp of a full grid), staged
   // tiles otherwise
-  if (elem_bytes == 1 && fast && K <= kHBins && n == 1 && total_units >= HR_STRIP_MIN_FACTOR * sms * kHW) {
-    const int grid = sms;
+  if (elem_bytes == 1 && fast && K <= kHBins && tab.n == 1 && total_units >= HR_STRIP_MIN_FACTOR * sms * kHW) {
+    const dim3 grid(sms);
     if (K < kHBins) {
       cudaFuncSetAttribute(hist_u8r_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem);
-      hist_u8r_kernel<true><<<grid, kHT, kHistSmem, st>>>(d_imgs, n, d_unit_start, total_units, K, slots, slot_bytes,
-                                                          lay, status);
-    } else {
-      cudaFuncSetAttribute(hist_u8r_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem);
-      hist_u8r_kernel<false><<<grid, kHT, kHistSmem, st>>>(d_imgs, n, d_unit_start, total_units, K, slots,
-                                                           slot_bytes, lay, status);
+      return launch_kernel(hist_u8r_kernel<true>, grid, dim3(kHT), kHistSmem, st, pdl, tab, total_units, K, slots,
+                           slot_bytes, lay, status);
     }
-    return cudaGetLastError();
+    cudaFuncSetAttribute(hist_u8r_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem);
+    return launch_kernel(hist_u8r_kernel<false>, grid, dim3(kHT), kHistSmem, st, pdl, tab, total_units, K, slots,
+                         slot_bytes, lay, status);
   }
   int grid = sms * ctas_per_sm;
   if (grid > total_tiles) grid = total_tiles;
@@ -827,36 +839,32 @@ cudaError_t launch_hist(const ImageDesc* d_imgs, int n, const int* d_tile_start,
   if (elem_bytes == 1 && fast) {
     const size_t smem_v = (size_t)2 * kWarps * K * sizeof(unsigned) + (size_t)kVH * kVTS + (size_t)2 * kVH * kRawRow;
     cudaFuncSetAttribute(hist_u8v_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_v);
-    hist_u8v_kernel<<<grid, kThreads, smem_v, st>>>(d_imgs, n, d_tile_start, total_tiles, K, slots, slot_bytes, lay,
-                                                    status);
-  } else if (elem_bytes == 1) {
-    cudaFuncSetAttribute(hist_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    hist_kernel<uint8_t><<<grid, kThreads, smem, st>>>(d_imgs, n, d_tile_start, total_tiles, K, slots, slot_bytes,
-                                                       lay, status);
-  } else {
-    cudaFuncSetAttribute(hist_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    hist_kernel<uint16_t><<<grid, kThreads, smem, st>>>(d_imgs, n, d_tile_start, total_tiles, K, slots, slot_bytes,
-                                                        lay, status);
+    return launch_kernel(hist_u8v_kernel, dim3(grid), dim3(kThreads), smem_v, st, pdl, tab, total_tiles, K, slots,
+                         slot_bytes, lay, status);
   }
-  return cudaGetLastError();
+  if (elem_bytes == 1) {
+    cudaFuncSetAttribute(hist_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return launch_kernel(hist_kernel<uint8_t>, dim3(grid), dim3(kThreads), smem, st, pdl, tab, total_tiles, K, slots,
+                         slot_bytes, lay, status);
+  }
+  cudaFuncSetAttribute(hist_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return launch_kernel(hist_kernel<uint16_t>, dim3(grid), dim3(kThreads), smem, st, pdl, tab, total_tiles, K, slots,
+                       slot_bytes, lay, status);
 }
 
-cudaError_t launch_apply(const ImageDesc* d_imgs, int n, const int* d_tile_start, int total_tiles, int elem_bytes,
-                         int K, uint8_t* slots, size_t slot_bytes, SlotLayout lay, unsigned* status, int grid,
-                         cudaStream_t st, bool fast) {
+cudaError_t launch_apply(const ImgTab& tab, int total_tiles, int elem_bytes, int K, uint8_t* slots, size_t slot_bytes,
+                         SlotLayout lay, unsigned* status, int grid, cudaStream_t st, bool fast, bool pdl) {
   const size_t smem = (size_t)((K * 2 + 15) & ~15) + (size_t)K * sizeof(float);
   if (grid > total_tiles) grid = total_tiles;
   if (grid < 1) grid = 1;
   if (elem_bytes == 1 && fast)
-    apply_u8v_kernel<<<grid, kThreads, 0, st>>>(d_imgs, n, d_tile_start, total_tiles, K, slots, slot_bytes, lay,
-                                                status);
-  else if (elem_bytes == 1)
-    apply_kernel<uint8_t><<<grid, kThreads, smem, st>>>(d_imgs, n, d_tile_start, total_tiles, K, slots, slot_bytes,
-                                                        lay, status);
-  else
-    apply_kernel<uint16_t><<<grid, kThreads, smem, st>>>(d_imgs, n, d_tile_start, total_tiles, K, slots,
-                                                         slot_bytes, lay, status);
-  return cudaGetLastError();
+    return launch_kernel(apply_u8v_kernel, dim3(grid), dim3(kThreads), 0, st, pdl, tab, total_tiles, K, slots,
+                         slot_bytes, lay, status);
+  if (elem_bytes == 1)
+    return launch_kernel(apply_kernel<uint8_t>, dim3(grid), dim3(kThreads), smem, st, pdl, tab, total_tiles, K, slots,
+                         slot_bytes, lay, status);
+  return launch_kernel(apply_kernel<uint16_t>, dim3(grid), dim3(kThreads), smem, st, pdl, tab, total_tiles, K, slots,
+                       slot_bytes, lay, status);
 }
 
 }  // namespace hr

@@ -20,6 +20,7 @@
 // others at three cluster barriers per iteration.  The summation order differs from a
 // left-to-right loop; sums of non-negative terms then agree to a few ulps per term.
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "hr_internal.cuh"
 
@@ -141,7 +142,7 @@ __device__ __forceinline__ int jstart_index(int i, int k, int K) {
   if (i == 0) return K;
   const int t = (2 * k - 1) * (K - 1), d = 2 * i;
   if (t > d * K) return K;
-  int q = __float2int_rz(__int2float_rn(t) / __int2float_rn(d));  // |error| < 1 here (q <= K)
+  int q = __float2int_rz(__fdividef(__int2float_rn(t), __int2float_rn(d)));  // within 1 of the quotient here
   int r = t - q * d;
   while (r < 0) { --q; r += d; }
   while (r >= d) { ++q; r -= d; }
@@ -153,11 +154,32 @@ struct JsIndex {
   int K;
   __device__ int operator()(int i, int k) const { return jstart_index(i, k, K); }
 };
-struct JsTable {  // per-context table for index_1 (Eq. 19)
-  const uint16_t* tab;
-  int K;
-  __device__ int operator()(int i, int k) const { return k >= K ? K : (int)tab[(size_t)i * (K + 1) + k]; }
-};
+// Exclusive block scan of one 64-bit value per thread; *total gets the sum.  r64 holds NW values.
+__device__ unsigned long long block_exscan64(unsigned long long v, unsigned long long* r64,
+                                             unsigned long long* total) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  unsigned long long x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(FULL, x, o);
+    if (l >= o) x += y;
+  }
+  __syncthreads();
+  if (l == 31) r64[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    unsigned long long s = l < NW ? r64[l] : 0ull;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(FULL, s, o);
+      if (l >= o) s += y;
+    }
+    if (l < NW) r64[l] = s;
+  }
+  __syncthreads();
+  const unsigned long long before = (w > 0 ? r64[w - 1] : 0ull) + x - v;
+  *total = r64[NW - 1];
+  __syncthreads();
+  return before;
+}
 
 // Exclusive block scan of one unsigned per thread; *total gets the sum.
 __device__ unsigned block_exscan(unsigned v, unsigned* red, unsigned* total) {
@@ -257,6 +279,11 @@ __device__ __forceinline__ void pull_even(const cg::cluster_group& cl, T* arr, i
     if (r != rank) arr[a] = cl.map_shared_rank(arr, r)[a];
   }
 }
+
+// Split cluster barrier: arrive (no ordering of this thread's memory accesses) and wait.  Every thread
+// of every CTA alternates the two; a CTA whose shared memory others read arrives once they are done.
+__device__ __forceinline__ void cluster_arrive_relaxed() { asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ long long global_ns() {
   long long t;
@@ -408,6 +435,8 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ F conv[2][NW];
   const cg::cluster_group cl = cg::this_cluster();
+  pdl_wait();     // the histogram pass before it on the stream has finished
+  pdl_trigger();  // the apply pass may be scheduled (it waits for this kernel)
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   const int K = A.K;
@@ -468,10 +497,15 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   const int k0 = tid * per, k1 = min(K, k0 + per);
   unsigned cr = 0, cl_ = 0, nsum = 0;
   for (int k = k0; k < k1; ++k) { cr += G[k] > 0u; cl_ += S[k] > 0u; nsum += S[k]; }
-  unsigned nRu, nLu, Nu;
-  unsigned offR = block_exscan(cr, ured, &nRu);
-  unsigned offL = block_exscan(cl_, ured, &nLu);
-  block_exscan(nsum, ured, &Nu);
+  // the three counts in one 64-bit scan: support sizes in bits 0-15 and 16-31 (at most K <= 4096
+  // each), pixels in bits 32-63
+  unsigned long long tot64;
+  const unsigned long long ex64 =
+      block_exscan64(cr | ((unsigned long long)cl_ << 16) | ((unsigned long long)nsum << 32),
+                     reinterpret_cast<unsigned long long*>(scr), &tot64);
+  unsigned offR = (unsigned)(ex64 & 0xffffu), offL = (unsigned)((ex64 >> 16) & 0xffffu);
+  const unsigned nRu = (unsigned)(tot64 & 0xffffu), nLu = (unsigned)((tot64 >> 16) & 0xffffu);
+  const unsigned Nu = (unsigned)(tot64 >> 32);
   for (int k = k0; k < k1; ++k) {
     if (G[k] > 0u) RI[offR++] = (uint16_t)k;
     posL[k] = (uint16_t)offL;
@@ -496,10 +530,15 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   stamp();
   // owner CTA of every class of the plan: rank r holds the classes whose first cell lies in
   // [cells r / C, cells (r + 1) / C) (rank 0 also those below, the last rank those above)
-  for (int c = tid; c < nL; c += NT) {
-    int r = C - 1;
-    while (r > 0 && cst[c] < (unsigned)(((unsigned long long)PP.cells * r) / C)) --r;
-    cowner[c] = (uint8_t)r;
+  {
+    __shared__ unsigned rank_lo[kMaxCluster];
+    if (tid < C) rank_lo[tid] = (unsigned)(((unsigned long long)PP.cells * tid) / C);
+    __syncthreads();
+    for (int c = tid; c < nL; c += NT) {
+      int r = C - 1;
+      while (r > 0 && cst[c] < rank_lo[r]) --r;
+      cowner[c] = (uint8_t)r;
+    }
   }
   // own rows and columns of the updates (contiguous slices)
   const int aA = (int)((long long)nR * rank / C), aB = (int)((long long)nR * (rank + 1) / C);
@@ -511,6 +550,9 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   // lane + shuffle-tree levels) x 64, and a lane's chain.  A CTA alone (batches: one image per CTA,
   // many rows each) uses 4.  (One image's arithmetic depends on C only
   // through these group sizes and the class split.)
+  // unrolling the Eq. 12/13 sums pays for the double-float form (FP32 pipes) and costs the FP64
+  // form more than it gains (measured on GB300: -3.7 us per 8K image without it)
+  constexpr int kSumUnroll = std::is_same<F, double>::value ? 1 : 4;
   auto group = [&](int own, int terms) {
     if (C == 1) return 4;
     int best = 32, cost = 1 << 30;
@@ -579,7 +621,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         F acc = 0.0;
         if (a < aB) {
           const int i = RI[a];
-#pragma unroll 4
+#pragma unroll kSumUnroll
           for (int b = gl; b < nL; b += GA) acc = fmaF(L2c[b], q[class_index(i, LJ[b], km1, cdiv)], acc);
         }
         for (int o = GA >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
@@ -621,7 +663,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         F acc = 0.0;
         if (b < bB) {
           const int j = LJ[b];
-#pragma unroll 4
+#pragma unroll kSumUnroll
           for (int a = gl; a < nR; a += GB) acc = fmaF(RRc[a], q[class_index(RI[a], j, km1, cdiv)], acc);
         }
         for (int o = GB >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
@@ -670,41 +712,43 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     stamp();
     if (done) break;
   }
-  // renormalised results of Algorithm 1 (Eq. 15 and Eq. 14 applied to the last iterate)
-  if (warp == 0) {
+  // Renormalised results of Algorithm 1 (Eq. 15 and Eq. 14 applied to the last iterate): R = scR R0
+  // and L = sl L0 with sl = N / sum L0.  The target below is bilinear in R and L, so its row pass
+  // runs on R0 and L0 while the last warp forms sl, and T takes the product of the scales at the end.
+  if (warp == NW - 1) {
     const F s1 = warp_sum(nL, [&](int b) { return L0[b]; });
     if (lane == 0) scal[4] = N * rcpF(s1);
   }
-  __syncthreads();
-  {
-    const F sl = scal[4];
-    for (int a = tid; a < nR; a += NT) R1[a] = scR * R0[a];
-    for (int b = tid; b < nL; b += NT) L1[b] = sl * L0[b];
-  }
-  __syncthreads();
-  Rc = R1;
-  Lc = L1;
+  Rc = R0;
+  Lc = L0;
 
   // ---- Eq. 17-20: enhanced histogram through the index_1 class map -----------------------------
   // The cells of class k in row i (Eq. 19) are the support columns of [js1(i, k), js1(i, k+1)),
   // so T_k = (1/N) sum_i R_i (sum of L over that run).  Row i meets the classes [k0, k1] of its
-  // first and last support column (index_1 grows with j, and is at most i).  Row pass: R_i times
-  // every run sum into the row's segment of the workspace (own rows; the class ranges go to every
-  // CTA); class pass: T_k as the sum over the rows whose range holds k, rows ascending (own classes).
-  const JsTable js1{A.jstart1, K};
-  unsigned* rk0 = csz;   // per row: first class (the class-plan arrays are free by now)
-  unsigned* rk1 = cst;   // per row: last class
-  F* seg = reinterpret_cast<F*>(slot + lay.list);  // row i's segment at i (i + 1) / 2, indexed by class
+  // first and last support column (index_1 grows with j, and is at most i).  Row pass (own rows):
+  // R_i times every run sum into the row's segment; partial pass: every CTA's T over its own rows,
+  // rows ascending; rank 0 then adds the CTAs' partial vectors in rank order.
+  unsigned* rk0 = csz;   // per own row: first class (the class-plan arrays are free by now)
+  unsigned* rk1 = cst;   // per own row: last class
+  // segments: row a at (a - aA) K in the shared memory the cell lists used (free now) when the own
+  // rows fit there, else row i at i (i + 1) / 2 in the workspace
+  F* seg_s = nullptr;
+  if (ob.s_part &&
+      (size_t)(aB - aA) * K * sizeof(F) <= (size_t)kPieceCap * (sizeof(F) + sizeof(uint2)) + (size_t)kListCap * sizeof(unsigned))
+    seg_s = static_cast<F*>(ob.s_part);  // (s_part, s_piece and s_list are contiguous)
+  F* seg_g = reinterpret_cast<F*>(slot + lay.list);
+  auto seg_of = [&](int a) { return seg_s ? seg_s + (size_t)(a - aA) * K : seg_g + (size_t)RI[a] * (RI[a] + 1) / 2; };
   {
     const int jmin = LJ[0], jmax = LJ[nL - 1];
     for (int a = aA + warp; a < aB; a += NW) {  // own rows, a warp each
       const int i = RI[a];
+      const uint16_t* jr = A.jstart1 + (size_t)i * (K + 1);  // js1(i, k), k <= K (entry K holds K)
       // classes of the first and last support column: k0 + 1 = #{k : js1(i, k) <= jmin}, likewise
       // k1 for jmax (js1 grows with k; boundaries read 32 at a time, counted by ballots)
       int c0 = 0, c1 = 0;
       for (int kb = 0; kb < K; kb += 32) {
         const int k = kb + lane;
-        const int v = k < K ? js1(i, k) : K + 1;
+        const int v = k < K ? (int)jr[k] : K + 1;
         const unsigned m1 = __ballot_sync(FULL, v <= jmax);
         c0 += __popc(__ballot_sync(FULL, v <= jmin));
         c1 += __popc(m1);
@@ -713,37 +757,69 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
       const int k0 = c0 - 1, k1 = min(c1 - 1, i);  // (index_1 never exceeds i: a_j <= 1)
       if (lane == 0) { rk0[a] = (unsigned)k0; rk1[a] = (unsigned)k1; }
       const F r = Rc[a];
-      F* out = seg + (size_t)i * (i + 1) / 2;  // row i meets at most classes 0 .. i
-      for (int k = k0 + lane; k <= k1; k += 32) {
-        const int p0 = posL[js1(i, k)], p1 = posL[js1(i, k + 1)];
+      F* out = seg_of(a);
+      // g lanes per class: a row with few classes has long runs, which g lanes sum in strides
+      int g = 32;
+      while (g > 1 && g * (k1 - k0 + 1) > 32) g >>= 1;
+      const int gi = lane / g, gl = lane % g, cpw = 32 / g;
+      for (int kk = k0; kk <= k1; kk += cpw) {
+        const int k = kk + gi;
         F sum = 0.0;
-        for (int b = p0; b < p1; ++b) sum += Lc[b];
-        out[k] = r * sum;
+        if (k <= k1) {
+          const int p0 = posL[jr[k]], p1 = posL[jr[k + 1]];
+          for (int b = p0 + gl; b < p1; b += g) sum += Lc[b];
+        }
+        for (int o = g >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+        if (gl == 0 && k <= k1) out[k] = r * sum;
       }
     }
-    __syncthreads();
-    push_slice(cl, rk0, aA, aB, C, rank);
-    push_slice(cl, rk1, aA, aB, C, rank);
   }
-  __threadfence();  // the segments are read by every CTA of the cluster
-  cl.sync();
-  stamp();
-  F* T = L2c;  // level-indexed target
-  {
-    const int kA = (int)((long long)K * rank / C), kB = (int)((long long)K * (rank + 1) / C);
-    for (int k = kA + warp; k < kB; k += NW) {
-      F sum = 0.0;
-      for (int a = lane; a < nR; a += 32)
-        if ((int)rk0[a] <= k && k <= (int)rk1[a]) sum += seg[(size_t)RI[a] * (RI[a] + 1) / 2 + k];
-      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
-      if (lane == 0) T[k] = sum * invN;  // the count matrix carries 1/N (Eq. 6)
+  __syncthreads();
+  F* Tp = L2c;  // this CTA's partial target (own rows)
+  // A few own rows (a cluster CTA): a branch per row, so whole warps skip the rows that miss their
+  // classes.  Many (a CTA alone): eight rows' loads in flight together.  Rows ascending either way.
+  const bool few_rows = aB - aA <= 32;
+  for (int k = tid; k < K; k += NT) {
+    F sum = 0.0;
+    if (few_rows) {
+      for (int a = aA; a < aB; ++a)
+        if ((int)rk0[a] <= k && k <= (int)rk1[a]) sum += seg_of(a)[k];
+    } else {
+      for (int a0 = aA; a0 < aB; a0 += 8) {
+        F v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int a = a0 + t;
+          v[t] = (a < aB && (int)rk0[a] <= k && k <= (int)rk1[a]) ? seg_of(a)[k] : (F)0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) sum += v[t];
+      }
     }
-    __syncthreads();
-    push_slice(cl, T, kA, kB, C, rank);
+    Tp[k] = sum;
   }
   cl.sync();
   stamp();
-  if (rank != 0) return;
+  if (rank != 0) {  // the partial is read by rank 0: stay until it has been
+    cluster_arrive_relaxed();
+    cluster_wait();
+    return;
+  }
+  const F sl = scal[4];
+  const F tscale = invN * (scR * sl);  // the count matrix carries 1/N (Eq. 6); R and L their scales
+  F* T = L2c;  // level-indexed target (rank 0, in place of its own partial)
+  for (int k = tid; k < K; k += NT) {
+    F v[kMaxCluster];
+#pragma unroll
+    for (int r = 1; r < kMaxCluster; ++r) v[r] = r < C ? cl.map_shared_rank(Tp, r)[k] : (F)0.0;
+    F sum = Tp[k];
+#pragma unroll
+    for (int r = 1; r < kMaxCluster; ++r) sum += v[r];
+    T[k] = sum * tscale;
+  }
+  __syncthreads();
+  cluster_arrive_relaxed();  // the other CTAs may leave (this CTA waits for that phase at its end)
+  stamp();
 
   // ---- histogram matching LUT (rank 0) -----------------------------------------------------------
   {
@@ -840,10 +916,15 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   // ---- results (level-indexed) -------------------------------------------------------------------
   for (int k = tid; k < K; k += NT) { Rout[k] = 0.0; Lout[k] = 0.0; Tout[k] = (double)T[k]; }
   __syncthreads();
-  for (int a = tid; a < nR; a += NT) Rout[RI[a]] = (double)Rc[a];
-  for (int b = tid; b < nL; b += NT) Lout[LJ[b]] = (double)Lc[b];
+  for (int a = tid; a < nR; a += NT) Rout[RI[a]] = (double)(scR * Rc[a]);
+  for (int b = tid; b < nL; b += NT) Lout[LJ[b]] = (double)(sl * Lc[b]);
   if (tid == 0) { misc[0] = it; misc[1] = nR; misc[2] = nL; misc[3] = (int)PP.cells; }
   stamp();
+  cluster_wait();  // (every CTA has passed the set-up, where all of them read H_C(S) and H_C(grad S))
+  if (A.zero_hist) {  // H_C(S) and H_C(grad S) (adjacent) cleared for the next call's histogram pass
+    unsigned* SG = reinterpret_cast<unsigned*>(slot + lay.S);
+    for (int k = tid; k < 2 * K; k += NT) SG[k] = 0u;
+  }
 }
 
 }  // namespace
@@ -886,7 +967,7 @@ int solve_cluster_size(size_t smem) {
 }
 
 template <typename F>
-cudaError_t launch_solve_t(const SolveArgs& a0, int n, int cluster, cudaStream_t st) {
+cudaError_t launch_solve_t(const SolveArgs& a0, int n, int cluster, cudaStream_t st, bool pdl) {
   // own cell lists in shared memory up to K = 1024 (beyond it they never fit a share); the
   // solver vectors there whenever the layout fits (for K = 4096: FP32 only)
   SolveArgs a = a0;
@@ -910,20 +991,22 @@ cudaError_t launch_solve_t(const SolveArgs& a0, int n, int cluster, cudaStream_t
   cfg.blockDim = dim3(NT);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = (unsigned)C;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pdl ? 2 : 1;
   return cudaLaunchKernelEx(&cfg, solve_kernel<F>, a);
 }
 
-cudaError_t launch_solve(const SolveArgs& a, int n, int cluster, cudaStream_t st) {
-  if (a.arith == kArithF32) return launch_solve_t<float>(a, n, cluster, st);
-  if (a.arith == kArithDF64) return launch_solve_t<df64>(a, n, cluster, st);
-  return launch_solve_t<double>(a, n, cluster, st);
+cudaError_t launch_solve(const SolveArgs& a, int n, int cluster, cudaStream_t st, bool pdl) {
+  if (a.arith == kArithF32) return launch_solve_t<float>(a, n, cluster, st, pdl);
+  if (a.arith == kArithDF64) return launch_solve_t<df64>(a, n, cluster, st, pdl);
+  return launch_solve_t<double>(a, n, cluster, st, pdl);
 }
 
 }  // namespace hr

@@ -19,8 +19,8 @@ constexpr int kStaticMaxK = 256;
 constexpr size_t kStaticBytes = size_t(1) << 20;
 constexpr int kMaxDevices = 64;
 
-// Workspace of every call, on every device: one image slot, the Eq. 19 boundary table, the
-// image descriptor, its tile start array and the status word.  Shared by all calls; it keeps the
+// Workspace of every call, on every device: one image slot, the Eq. 19 boundary table and the
+// status word.  Shared by all calls; it keeps the
 // previous call's contents, so each call clears what must start at zero.
 __device__ __align__(256) unsigned char g_scratch[kStaticBytes];
 
@@ -55,9 +55,7 @@ extern "C" hr_status histretinex_enhance_noalloc(const hr_params* p, const void*
   const int K = p->K;
   const hr::SlotLayout lay = hr::make_layout(K);
   const size_t off_table = align256(lay.bytes);
-  const size_t off_desc = align256(off_table + sizeof(uint16_t) * (size_t)K * (K + 1));
-  const size_t off_tiles = off_desc + align256(sizeof(hr::ImageDesc));
-  const size_t off_status = off_tiles + 256;
+  const size_t off_status = align256(off_table + sizeof(uint16_t) * (size_t)K * (K + 1));
   if (off_status + 256 > kStaticBytes) return HR_ERR_UNSUPPORTED;
 
   int dev = 0;
@@ -84,26 +82,22 @@ extern "C" hr_status histretinex_enhance_noalloc(const hr_params* p, const void*
     ds.table_K = K;
     ds.table_gamma = p->gamma;
   }
-  const hr::ImageDesc desc{static_cast<const uint8_t*>(d_in), static_cast<uint8_t*>(d_out), width, height,
-                           (long long)in_pitch, (long long)out_pitch};
+  hr::ImgTab tab{};  // the image travels in the kernel parameters
+  tab.n = 1;
+  tab.one = hr::ImageDesc{static_cast<const uint8_t*>(d_in), static_cast<uint8_t*>(d_out), width, height,
+                          (long long)in_pitch, (long long)out_pitch};
   const int tiles = hr::tiles_of(width, height), units = hr::strips_of(width, height);
-  const int tile_start[4] = {0, tiles, 0, units};  // tile list, then strip list
-  cudaError_t e = cudaMemcpyAsync(base + off_desc, &desc, sizeof(desc), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(base + off_tiles, tile_start, sizeof(tile_start), cudaMemcpyHostToDevice, st);
   // what must start at zero: the two histograms and the status word
-  if (e == cudaSuccess) e = cudaMemsetAsync(base + lay.S, 0, (size_t)2 * K * sizeof(unsigned), st);
+  cudaError_t e = cudaMemsetAsync(base + lay.S, 0, (size_t)2 * K * sizeof(unsigned), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(base + off_status, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return HR_ERR_CUDA;
 
   const bool fast_in = elem_bytes == 1 && ((uintptr_t)d_in % 16 == 0) && (in_pitch % 16 == 0);
   const bool fast_out = fast_in && ((uintptr_t)d_out % 16 == 0) && (out_pitch % 16 == 0);
-  auto* d_desc = reinterpret_cast<const hr::ImageDesc*>(base + off_desc);
-  auto* d_tiles = reinterpret_cast<const int*>(base + off_tiles);
   auto* d_status = reinterpret_cast<unsigned*>(base + off_status);
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return HR_ERR_CUDA;
-  e = hr::launch_hist(d_desc, 1, d_tiles, tiles, d_tiles + 2, units, elem_bytes, K, base, lay.bytes, lay, d_status,
-                      sms, 8, st, fast_in);
+  e = hr::launch_hist(tab, tiles, units, elem_bytes, K, base, lay.bytes, lay, d_status, sms, 8, st, fast_in, true);
   if (e != cudaSuccess) return HR_ERR_CUDA;
   hr::SolveArgs a{};
   a.K = K;
@@ -119,8 +113,8 @@ extern "C" hr_status histretinex_enhance_noalloc(const hr_params* p, const void*
   a.status = d_status;
   a.profile = 0;
   a.arith = p->precision == HR_PREC_FP32 ? hr::kArithF32 : (p->precision == HR_PREC_DF64 ? hr::kArithDF64 : hr::kArithF64);
-  e = hr::launch_solve(a, 1, 16, st);
+  e = hr::launch_solve(a, 1, 16, st, false);
   if (e != cudaSuccess) return HR_ERR_CUDA;
-  e = hr::launch_apply(d_desc, 1, d_tiles, tiles, elem_bytes, K, base, lay.bytes, lay, d_status, sms * 8, st, fast_out);
+  e = hr::launch_apply(tab, tiles, elem_bytes, K, base, lay.bytes, lay, d_status, sms * 8, st, fast_out, true);
   return e == cudaSuccess ? HR_OK : HR_ERR_CUDA;
 }
