@@ -89,8 +89,9 @@ typedef struct hr_ctx hr_ctx;
 /* Launch shapes (not part of the paper's method).  hist_ctas_per_sm, apply_ctas_per_sm: the
  * persistent grids of the two pixel passes are SMs x this many CTAs (1..32; default 8; the 8-bit
  * histogram kernel for one large image with 16-byte aligned rows runs one CTA per SM instead);
- * solve_cluster: CTAs per thread-block cluster for a single image's solve (1, 2, 4, 8 or 16;
- * default 16, lowered automatically when that cluster cannot be resident); use_graph: 1 to
+ * solve_cluster: CTAs per thread-block cluster of an image's solve (1, 2, 4, 8 or 16; default 16,
+ * lowered automatically when that cluster cannot be resident; a batch of n images uses at most
+ * SMs / n, rounded down to a power of two, so that it runs in one wave); use_graph: 1 to
  * capture enhance_batch's launches into a CUDA graph that is replayed while the batch's geometry
  * (image count, sizes, element size, alignment) is unchanged (default 1).  Stage timing is not
  * recorded for graph replays.  pdl: which kernels are programmatic dependent launches (bit 0 the
@@ -128,10 +129,12 @@ hr_status histretinex_enhance(hr_ctx* ctx, const void* d_in, void* d_out, int wi
  * persistent kernels walk per-image work queues, so images of mixed sizes share the GPU; the
  * launches are captured into a CUDA graph and replayed while the batch geometry is unchanged.
  * The arrays are HOST arrays of length n (d_in[i], d_out[i] are device pointers).
- * Every image is solved by one CTA, so its result (pixels, LUT and FP64 histograms) is
- * bit-identical whatever else is in the batch, including a batch of one.  Against
- * histretinex_enhance (which solves one image on a CTA cluster, summing in another order) the
- * pixels and LUT agree and the FP64 histograms agree to rounding. */
+ * Every image is solved by a cluster of C CTAs, C the largest power of two up to the tuned
+ * solve_cluster with n C <= SMs (one CTA each for large batches).  An image's result (pixels,
+ * LUT and FP64 histograms) depends only on the image and C: it is bit-identical whatever else is
+ * in the batch for batches of the same C, and a batch of one matches histretinex_enhance.
+ * Between different C the FP64 histograms agree to rounding (they are summed in another order)
+ * and the pixels and LUT agree. */
 hr_status histretinex_enhance_batch(hr_ctx* ctx, int n, const void* const* d_in, void* const* d_out,
                                     const int* width, const int* height, const size_t* in_pitch,
                                     const size_t* out_pitch, int elem_bytes, void* stream);

@@ -212,7 +212,7 @@ hr_status fold_timing(hr_ctx* c, int i) {
 // The pipeline's device work on one stream: zero the histograms (unless the previous solves left
 // them zero), histogram pass, solve, apply.  ev (optional): four events recorded around the three
 // stages.
-cudaError_t enqueue_stages(hr_ctx* c, const ImgTab& tab, int total, int units, int elem_bytes, bool fast_in,
+cudaError_t enqueue_stages(hr_ctx* c, const ImgTab& tab, int total, int units, int interior, int elem_bytes, bool fast_in,
                            bool fast_out, bool batched, bool zero, cudaStream_t st, cudaEvent_t* ev) {
   const int K = c->p.K, n = tab.n;
   const int pdl = c->tune.pdl;  // bit 0: histogram pass, bit 1: solve, bit 2: apply pass
@@ -224,7 +224,7 @@ cudaError_t enqueue_stages(hr_ctx* c, const ImgTab& tab, int total, int units, i
     if (e != cudaSuccess) return e;
   }
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-  e = hr::launch_hist(tab, total, units, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay, c->d_status, c->sm_count,
+  e = hr::launch_hist(tab, total, units, interior, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay, c->d_status, c->sm_count,
                       c->tune.hist_ctas_per_sm, st, fast_in, (pdl & 1) != 0);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
@@ -244,7 +244,17 @@ cudaError_t enqueue_stages(hr_ctx* c, const ImgTab& tab, int total, int units, i
   a.profile = debug ? 1 : 0;
   a.zero_hist = debug ? 0 : 1;
   a.arith = c->p.precision == HR_PREC_FP32 ? hr::kArithF32 : (c->p.precision == HR_PREC_DF64 ? hr::kArithDF64 : hr::kArithF64);
-  e = hr::launch_solve(a, n, batched ? 1 : c->tune.solve_cluster, st, (pdl & 2) != 0);
+  // CTAs per image: the tuned cluster for one image; for a batch as many as keep all images in
+  // one wave (the largest power of two with n C <= SMs, at most the tuned cluster), so a batch
+  // of a few images runs as fast as its images would alone and a large one on one CTA each
+  int C = c->tune.solve_cluster;
+  if (batched) {
+    const int per = c->sm_count / n;
+    int p2 = 1;
+    while (2 * p2 <= per) p2 *= 2;
+    C = p2 < C ? p2 : C;
+  }
+  e = hr::launch_solve(a, n, C, st, (pdl & 2) != 0);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
   e = hr::launch_apply(tab, total, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay, c->d_status,
@@ -265,7 +275,7 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
   const int K = c->p.K;
   if (elem_bytes != 1 && elem_bytes != 2) return HR_ERR_INVALID_ARG;
   if (elem_bytes == 1 && K > 256) return HR_ERR_INVALID_ARG;
-  long long total = 0, units = 0;
+  long long total = 0, units = 0, interior = 0;
   for (int i = 0; i < n; ++i) {
     const ImageDesc& d = imgs[i];
     if (!d.in || !d.out || d.W < 1 || d.H < 1) return HR_ERR_INVALID_ARG;
@@ -274,6 +284,7 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
     if ((long long)d.W * d.H >= (1LL << 31)) return HR_ERR_UNSUPPORTED;
     total += hr::tiles_of(d.W, d.H);
     units += hr::strips_of(d.W, d.H);
+    interior += hr::interior_strips_of(d.W, d.H);
   }
   if (total >= (1LL << 31) || units >= (1LL << 31)) return HR_ERR_UNSUPPORTED;
   // 8-bit fast paths need every row 16-byte aligned (input for the histogram pass, both for apply)
@@ -345,7 +356,7 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        e = enqueue_stages(c, tab, (int)total, (int)units, elem_bytes, fast_in, fast_out, batched, debug, cap, nullptr);
+        e = enqueue_stages(c, tab, (int)total, (int)units, (int)interior, elem_bytes, fast_in, fast_out, batched, debug, cap, nullptr);
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         if (e == cudaSuccess) e = e2;
       }
@@ -375,7 +386,7 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
     c->ev_used[i] = true;
   }
   const bool zero = debug || c->hist_clean < n;
-  const cudaError_t e = enqueue_stages(c, tab, (int)total, (int)units, elem_bytes, fast_in, fast_out, batched, zero, st, ev);
+  const cudaError_t e = enqueue_stages(c, tab, (int)total, (int)units, (int)interior, elem_bytes, fast_in, fast_out, batched, zero, st, ev);
   note_hist_state(c, n, e == cudaSuccess);
   if (e != cudaSuccess) return cuda_fail(e);
   c->launches += 3;

@@ -123,10 +123,12 @@ struct SolveArgs {
 // Launchers (return cudaError_t of the launch).  pdl: programmatic dependent launch (the kernel
 // may be scheduled before the previous kernel on the stream has finished; it waits for it on the
 // device before touching any data).
-// The histogram pass walks the tile list or, for one large 8-bit image with aligned rows, the
-// strip list (kStripW x kBandH units); both lists are given, with their totals.  Tile kernels
+// The histogram pass walks the tile list or, for enough 8-bit images with aligned rows, the
+// strip list (kStripW x kBandH units); both lists are given, with their totals and the number of
+// interior strips (strips that cross no right or bottom image edge).  Tile kernels
 // run sms x ctas_per_sm CTAs, the strip kernel one CTA per SM.
-cudaError_t launch_hist(const ImgTab& tab, int total_tiles, int total_units, int elem_bytes, int K, uint8_t* slots,
+cudaError_t launch_hist(const ImgTab& tab, int total_tiles, int total_units, int interior_units, int elem_bytes,
+                        int K, uint8_t* slots,
                         size_t slot_bytes, SlotLayout lay, unsigned* status, int sms, int ctas_per_sm,
                         cudaStream_t st, bool fast, bool pdl);
 cudaError_t launch_solve(const SolveArgs& a, int n, int cluster, cudaStream_t st, bool pdl);
@@ -143,5 +145,6 @@ inline int tiles_of(int W, int H) { return ((W + kTileW - 1) / kTileW) * ((H + k
 constexpr int kStripW = 512;
 constexpr int kBandH = 8;
 inline int strips_of(int W, int H) { return ((W + kStripW - 1) / kStripW) * ((H + kBandH - 1) / kBandH); }
+inline int interior_strips_of(int W, int H) { return (W / kStripW) * (H / kBandH); }
 
 }  // namespace hr

@@ -465,7 +465,7 @@ __device__ __noinline__ bool hist_tile_edge(const LaneTile g, int yb, int mclip,
 }
 
 template <bool kClamp>
-__global__ void __launch_bounds__(kHT, 1) hist_u8r_kernel(const ImgTab tab, int total, int K,
+__global__ void __launch_bounds__(kHT, 1) hist_u8r_kernel(const ImgTab tab, int total, int all_edge, int K,
                                                          uint8_t* slots, size_t slot_bytes, SlotLayout lay,
                                                          unsigned* status) {
   pdl_wait();     // the previous kernel on the stream has finished
@@ -509,30 +509,52 @@ __global__ void __launch_bounds__(kHT, 1) hist_u8r_kernel(const ImgTab tab, int 
     }
     __syncwarp();
   };
+  // Units of one image: first its interior strips (row-major), then the edge strips (the right
+  // column, then the bottom band), so a warp runs one code path for long stretches: alternating
+  // paths thrash the instruction cache.  When edge strips are many (batches of small images),
+  // all strips take the edge path (all_edge).  A warp's units only grow, so the image is looked
+  // up again only when a unit passes the current image's end.
+  int img_start = 0, img_end = 0, nx = 0, nxi = 0, nyi = 0, n_int = 0, n_right = 0;
   for (;;) {
     int t = 0;
     if (lane == 0) t = atomicAdd(&next_tile, 1);
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= t1) break;
-    const int img = image_of_tile(unit_start, n, t);
-    if (img != cur) {
-      if (cur >= 0) flush_warp(cur);
+    if (cur < 0 || t >= img_end) {
+      const int img = image_of_tile(unit_start, n, t);
+      if (cur >= 0 && img != cur) flush_warp(cur);
       cur = img;
+      const ImageDesc im = tab.desc(img);
+      g.in = im.in;
+      g.pitch = im.in_pitch;
+      g.W = im.W;
+      g.H = im.H;
+      img_start = tab.unit0(img);
+      img_end = n == 1 ? total : tab.unit0(img + 1);
+      nx = (g.W + kStripW - 1) / kStripW;
+      nxi = g.W / kStripW;
+      nyi = g.H / kBandH;
+      n_int = nxi * nyi;
+      n_right = (nx - nxi) * nyi;
     }
-    const ImageDesc im = tab.desc(img);
-    g.in = im.in;
-    g.pitch = im.in_pitch;
-    g.W = im.W;
-    g.H = im.H;
-    const int lt = t - tab.unit0(img);
-    const int strips_x = (g.W + kStripW - 1) / kStripW;
-    g.x0 = (lt % strips_x) * kStripW;
-    const int y0 = (lt / strips_x) * kBandH;
+    const int lt = t - img_start;
+    int sx, sy;
+    if (lt < n_int) {
+      sy = lt / nxi;
+      sx = lt - sy * nxi;
+    } else if (lt - n_int < n_right) {
+      sx = nxi;
+      sy = lt - n_int;
+    } else {
+      sx = lt - n_int - n_right;
+      sy = nyi;
+    }
+    g.x0 = sx * kStripW;
+    const int y0 = sy * kBandH;
     g.xc = g.x0 + 16 * g.lx;
     g.cnt = g.W - g.xc;
     const int yb = y0 - 1;
-    const bool edge = g.x0 + kStripW > g.W || y0 + kBandH > g.H;
-    if (edge) bad |= hist_tile_edge<kClamp>(g, yb, mclip, kk, hs_sh, hg_adj);
+    if (all_edge || lt >= n_int) bad |= hist_tile_edge<kClamp>(g, yb, mclip, kk, hs_sh, hg_adj);
     else bad |= hist_tile<false, kClamp>(g, yb, mclip, kk, hs_sh, hg_adj);
   }
   // the warps' last images: sum the warps that share an image, one global add per level
@@ -815,22 +837,24 @@ __global__ void __launch_bounds__(kThreads) apply_u8v_kernel(const ImgTab tab, i
 
 }  // namespace
 
-cudaError_t launch_hist(const ImgTab& tab, int total_tiles, int total_units, int elem_bytes, int K, uint8_t* slots,
+cudaError_t launch_hist(const ImgTab& tab, int total_tiles, int total_units, int interior_units, int elem_bytes,
+                        int K, uint8_t* slots,
                         size_t slot_bytes, SlotLayout lay, unsigned* status, int sms, int ctas_per_sm,
                         cudaStream_t st, bool fast, bool pdl) {
   const int copies = K <= 256 ? kWarps : 1;
   const size_t smem = (size_t)2 * copies * K * sizeof(unsigned) + (size_t)kVH * kVW * sizeof(unsigned short);
-  // strips for one large image (at least HR_STRIP_MIN_FACTOR per warp of a full grid), staged
-  // tiles otherwise
-  if (elem_bytes == 1 && fast && K <= kHBins && tab.n == 1 && total_units >= HR_STRIP_MIN_FACTOR * sms * kHW) {
+  // strips when the launch has at least HR_STRIP_MIN_FACTOR of them per warp of a full grid (one
+  // large image or a large batch), staged tiles otherwise
+  if (elem_bytes == 1 && fast && K <= kHBins && total_units >= HR_STRIP_MIN_FACTOR * sms * kHW) {
     const dim3 grid(sms);
+    const int all_edge = 8LL * interior_units < 7LL * total_units ? 1 : 0;  // more than 1/8 edge strips
     if (K < kHBins) {
       cudaFuncSetAttribute(hist_u8r_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem);
-      return launch_kernel(hist_u8r_kernel<true>, grid, dim3(kHT), kHistSmem, st, pdl, tab, total_units, K, slots,
+      return launch_kernel(hist_u8r_kernel<true>, grid, dim3(kHT), kHistSmem, st, pdl, tab, total_units, all_edge, K, slots,
                            slot_bytes, lay, status);
     }
     cudaFuncSetAttribute(hist_u8r_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem);
-    return launch_kernel(hist_u8r_kernel<false>, grid, dim3(kHT), kHistSmem, st, pdl, tab, total_units, K, slots,
+    return launch_kernel(hist_u8r_kernel<false>, grid, dim3(kHT), kHistSmem, st, pdl, tab, total_units, all_edge, K, slots,
                          slot_bytes, lay, status);
   }
   int grid = sms * ctas_per_sm;

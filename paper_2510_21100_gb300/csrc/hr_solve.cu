@@ -150,9 +150,25 @@ __device__ __forceinline__ int jstart_index(int i, int k, int K) {
   return q < K ? q : K;
 }
 
+// The same boundary for row a (level i = RI[a]) with the division exact through a per-row
+// reciprocal: mg[a] = ceil(2^64 / (2 i)), so floor(t / (2 i)) = high 64 bits of t mg[a] for every
+// t < 2^32 (the reciprocal's excess below 1 moves t mg[a] / 2^64 by under t / 2^64, less than the
+// distance 1 / (2 i) from t / (2 i) to the next integer).  mg == nullptr: the float quotient.
 struct JsIndex {
   int K;
-  __device__ int operator()(int i, int k) const { return jstart_index(i, k, K); }
+  const uint16_t* RI;
+  const unsigned long long* mg;
+  __device__ int operator()(int a, int k) const {
+    const int i = RI[a];
+    if (!mg) return jstart_index(i, k, K);
+    if (k <= 0) return 0;
+    if (i == 0) return K;
+    const unsigned t = (unsigned)((2 * k - 1) * (K - 1)), d = 2u * (unsigned)i;
+    if (t > d * (unsigned)K) return K;
+    unsigned q = (unsigned)__umul64hi((unsigned long long)t, mg[a]);
+    q += (t - q * d) != 0u;  // ceil
+    return q < (unsigned)K ? (int)q : K;
+  }
 };
 // Exclusive block scan of one 64-bit value per thread; *total gets the sum.  r64 holds NW values.
 __device__ unsigned long long block_exscan64(unsigned long long v, unsigned long long* r64,
@@ -325,8 +341,7 @@ __device__ ClassPlan plan_classes(const cg::cluster_group& cl, int nR, int ncls,
     unsigned s = 0;
 #pragma unroll 4
     for (int a = l; a < nR; a += 32) {
-      const int i = RI[a];
-      s += (unsigned)(posL[js(i, k + 1)] - posL[js(i, k)]);
+      s += (unsigned)(posL[js(a, k + 1)] - posL[js(a, k)]);
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
     if (l == 0) csz[c] = s;
@@ -364,9 +379,8 @@ __device__ ClassPlan plan_classes(const cg::cluster_group& cl, int nR, int ncls,
       const int a = a0 + l;
       int lo_b = 0, cnt = 0;
       if (a < nR) {
-        const int i = RI[a];
-        lo_b = posL[js(i, k)];
-        cnt = posL[js(i, k + 1)] - lo_b;
+        lo_b = posL[js(a, k)];
+        cnt = posL[js(a, k + 1)] - lo_b;
       }
       unsigned x = (unsigned)cnt;
       for (int o = 1; o < 32; o <<= 1) {
@@ -525,7 +539,14 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   // ---- Eq. 11 classes that matter (S_k > 0): plan and own cell lists -------------------------
   cl.sync();  // every CTA of the cluster has started before any distributed shared memory access
   stamp();
-  const ClassPlan PP = plan_classes(cl, nR, nL, RI, posL, JsIndex{K}, [&](int c) { return (int)LJ[c]; }, csz, cst,
+  // per-row reciprocals of the Eq. 11 boundary division, in the LUT scan buffer (free until then)
+  unsigned long long* mg = nullptr;
+  if (nR <= NT) {
+    mg = reinterpret_cast<unsigned long long*>(scr);
+    for (int a = tid; a < nR; a += NT) mg[a] = RI[a] ? ~0ull / (2ull * RI[a]) + 1ull : 0ull;
+    __syncthreads();
+  }
+  const ClassPlan PP = plan_classes(cl, nR, nL, RI, posL, JsIndex{K, RI, mg}, [&](int c) { return (int)LJ[c]; }, csz, cst,
                                     pst, ob, ured, rank, C);
   stamp();
   // owner CTA of every class of the plan: rank r holds the classes whose first cell lies in
@@ -726,16 +747,26 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   // The cells of class k in row i (Eq. 19) are the support columns of [js1(i, k), js1(i, k+1)),
   // so T_k = (1/N) sum_i R_i (sum of L over that run).  Row i meets the classes [k0, k1] of its
   // first and last support column (index_1 grows with j, and is at most i).  Row pass (own rows):
-  // R_i times every run sum into the row's segment; partial pass: every CTA's T over its own rows,
-  // rows ascending; rank 0 then adds the CTAs' partial vectors in rank order.
+  // R_i times every run sum; partial pass: every CTA's T over its own rows; rank 0 then adds the
+  // CTAs' partial vectors in rank order.
   unsigned* rk0 = csz;   // per own row: first class (the class-plan arrays are free by now)
   unsigned* rk1 = cst;   // per own row: last class
-  // segments: row a at (a - aA) K in the shared memory the cell lists used (free now) when the own
-  // rows fit there, else row i at i (i + 1) / 2 in the workspace
+  // Where the row pass puts its sums, in the shared memory the cell lists used (free now) when
+  // they fit, else in the workspace: a few own rows (cluster CTAs) each get a segment; many (a CTA
+  // alone) add into per-warp partial targets instead (a warp's rows in order, then the warps in
+  // order), which spares the pass over all rows per class.
+  const size_t room = (size_t)kPieceCap * (sizeof(F) + sizeof(uint2)) + (size_t)kListCap * sizeof(unsigned);
+  const bool few_rows = aB - aA <= 32;
   F* seg_s = nullptr;
-  if (ob.s_part &&
-      (size_t)(aB - aA) * K * sizeof(F) <= (size_t)kPieceCap * (sizeof(F) + sizeof(uint2)) + (size_t)kListCap * sizeof(unsigned))
-    seg_s = static_cast<F*>(ob.s_part);  // (s_part, s_piece and s_list are contiguous)
+  F* wacc = nullptr;
+  if (ob.s_part) {  // (s_part, s_piece and s_list are contiguous)
+    if (few_rows && (size_t)(aB - aA) * K * sizeof(F) <= room) seg_s = static_cast<F*>(ob.s_part);
+    if (!few_rows && (size_t)NW * K * sizeof(F) <= room) wacc = static_cast<F*>(ob.s_part);
+  }
+  if (wacc) {
+    for (int e = tid; e < NW * K; e += NT) wacc[e] = (F)0.0;
+    __syncthreads();
+  }
   F* seg_g = reinterpret_cast<F*>(slot + lay.list);
   auto seg_of = [&](int a) { return seg_s ? seg_s + (size_t)(a - aA) * K : seg_g + (size_t)RI[a] * (RI[a] + 1) / 2; };
   {
@@ -757,7 +788,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
       const int k0 = c0 - 1, k1 = min(c1 - 1, i);  // (index_1 never exceeds i: a_j <= 1)
       if (lane == 0) { rk0[a] = (unsigned)k0; rk1[a] = (unsigned)k1; }
       const F r = Rc[a];
-      F* out = seg_of(a);
+      F* out = wacc ? wacc + (size_t)warp * K : seg_of(a);
       // g lanes per class: a row with few classes has long runs, which g lanes sum in strides
       int g = 32;
       while (g > 1 && g * (k1 - k0 + 1) > 32) g >>= 1;
@@ -770,21 +801,23 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
           for (int b = p0 + gl; b < p1; b += g) sum += Lc[b];
         }
         for (int o = g >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
-        if (gl == 0 && k <= k1) out[k] = r * sum;
+        if (gl == 0 && k <= k1) {
+          if (wacc) out[k] += r * sum;
+          else out[k] = r * sum;
+        }
       }
     }
   }
   __syncthreads();
   F* Tp = L2c;  // this CTA's partial target (own rows)
-  // A few own rows (a cluster CTA): a branch per row, so whole warps skip the rows that miss their
-  // classes.  Many (a CTA alone): eight rows' loads in flight together.  Rows ascending either way.
-  const bool few_rows = aB - aA <= 32;
   for (int k = tid; k < K; k += NT) {
     F sum = 0.0;
-    if (few_rows) {
+    if (wacc) {
+      for (int w = 0; w < NW; ++w) sum += wacc[w * K + k];
+    } else if (few_rows) {  // a branch per row: whole warps skip the rows that miss their classes
       for (int a = aA; a < aB; ++a)
         if ((int)rk0[a] <= k && k <= (int)rk1[a]) sum += seg_of(a)[k];
-    } else {
+    } else {  // eight rows' loads in flight together, rows ascending
       for (int a0 = aA; a0 < aB; a0 += 8) {
         F v[8];
 #pragma unroll
@@ -978,11 +1011,11 @@ cudaError_t launch_solve_t(const SolveArgs& a0, int n, int cluster, cudaStream_t
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(solve_kernel<F>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
-  // one image: the requested cluster (vectors must be in shared memory), capped at what can be
-  // resident; batches: one CTA per image
+  // the requested cluster per image (vectors must be in shared memory), capped at what can be
+  // resident
   static int cached_K = -1, cached_max = 1;
   int C = 1;
-  if (n == 1 && a.vec_in_smem && cluster > 1) {
+  if (a.vec_in_smem && cluster > 1) {
     if (cached_K != a.K) { cached_max = solve_cluster_size<F>(smem); cached_K = a.K; }
     C = cluster < cached_max ? cluster : cached_max;
   }

@@ -97,7 +97,7 @@ extern "C" hr_status histretinex_enhance_noalloc(const hr_params* p, const void*
   auto* d_status = reinterpret_cast<unsigned*>(base + off_status);
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return HR_ERR_CUDA;
-  e = hr::launch_hist(tab, tiles, units, elem_bytes, K, base, lay.bytes, lay, d_status, sms, 8, st, fast_in, true);
+  e = hr::launch_hist(tab, tiles, units, hr::interior_strips_of(width, height), elem_bytes, K, base, lay.bytes, lay, d_status, sms, 8, st, fast_in, true);
   if (e != cudaSuccess) return HR_ERR_CUDA;
   hr::SolveArgs a{};
   a.K = K;

@@ -132,7 +132,8 @@ def test_invalid_arguments(hr):
 
 def test_batch_equals_single_images(hr):
     """Each image of a mixed-size batch gets the pixels and LUT it gets alone; its FP64 histograms
-    agree within RTOL (one image alone runs on a CTA cluster, a batch image on one CTA)."""
+    agree within RTOL (here both run on 16-CTA clusters; large batches run on smaller clusters or
+    one CTA per image and sum in another order)."""
     import torch
     from gpu_util import assert_close
     ctx, po = ctx_for(hr)
@@ -153,8 +154,24 @@ def test_batch_equals_single_images(hr):
         compare_to_oracle(im, out_b, batch_dbg[i], po)
 
 
+def test_batch_of_one_is_the_single_image_call(hr):
+    """A batch of one image runs the single-image pipeline's kernels with the same cluster: the
+    same bits throughout."""
+    import torch
+    ctx, _ = ctx_for(hr)
+    img = synth.low_light_image(1280, 720, seed=4343)
+    d = torch.from_numpy(img).cuda()
+    out_b = ctx.enhance_batch([d])[0].cpu().numpy()
+    dbg_b = ctx.debug(0)
+    out_s, dbg_s = run_gpu(ctx, img)
+    assert np.array_equal(out_b, out_s)
+    for k in ("S", "G", "R", "L", "T", "lut"):
+        assert np.array_equal(dbg_b[k], dbg_s[k]), k
+
+
 def test_batch_result_independent_of_batch_composition(hr):
-    """In the batched path an image's result is bit-identical whatever else is in the batch."""
+    """In the batched path an image's result is bit-identical whatever else is in the batch (for
+    batches whose images get the same cluster size: here 16 CTAs)."""
     import torch
     ctx, _ = ctx_for(hr)
     target = synth.low_light_image(300, 200, seed=4242)
@@ -170,6 +187,33 @@ def test_batch_result_independent_of_batch_composition(hr):
     assert np.array_equal(o1, o2)
     for k in ("S", "G", "R", "L", "T", "lut"):
         assert np.array_equal(d1[k], d2[k]), k
+
+
+def test_large_batch_takes_strip_histograms(hr):
+    """A batch with enough 512 x 8 strips for the strip histogram kernel, which takes each image's
+    interior strips first and then its right column and bottom band: every image gets the
+    histograms, LUT and pixels it gets alone, and a few are checked against the oracle."""
+    import torch
+    from gpu_util import assert_close
+    ctx, po = ctx_for(hr)
+    sizes = [(1500, 1000), (1283, 725), (700, 333), (512, 480), (1024, 769), (95, 33), (1, 1), (2047, 1031)] * 4
+    assert sum(-(-w // 512) * -(-h // 8) for w, h in sizes) >= 2 * 152 * 16
+    imgs = [synth.low_light_image(w, h, seed=5100 + i) for i, (w, h) in enumerate(sizes)]
+    dins = [hr.to_device_aligned(im) for im in imgs]
+    douts = [hr.aligned_empty(h, w) for (w, h) in sizes]
+    ctx.enhance_batch(dins, douts)
+    ctx.check()
+    batch = [(douts[i].cpu().numpy(), ctx.debug(i)) for i in range(len(imgs))]
+    for i, im in enumerate(imgs):
+        out_b, dbg_b = batch[i]
+        out_s, dbg_s = run_gpu(ctx, im)
+        for k in ("S", "G", "lut"):
+            assert np.array_equal(dbg_b[k], dbg_s[k]), (i, k)
+        for k in ("R", "L", "T"):
+            assert_close(dbg_b[k], dbg_s[k], k)
+        assert np.array_equal(out_b, out_s), i
+    for i in (0, 2, 7):
+        compare_to_oracle(imgs[i], batch[i][0], batch[i][1], po)
 
 
 def test_host_entry_point_matches_device_path(hr):
