@@ -362,7 +362,8 @@ def main():
     stages = {"hist": h_ms, "solve": s_ms, "apply": a_ms}
     dom = max(stages, key=stages.get)
     fp64_peak = 1250.0  # GFLOP/s: nominal GB300 FP64 from the profiling recipe (probe measured 1190-1200)
-    hist_name = "hist_u8r_kernel" if W * H >= 2 * 16 * 152 * 4096 else "hist_u8v_kernel"
+    # the strip kernel runs when the image has at least 2 strips (512 x 4 pixels) per warp of a full grid
+    hist_name = "hist_u8r_kernel" if -(-W // 512) * -(-H // 4) >= 2 * 16 * 152 else "hist_u8v_kernel"
     kern = {
         "hist": {"kernel": hist_name, "bound": "hbm", "achieved": hist_bytes / (h_ms / 1e3) / 1e9,
                  "peak": pk["hbm_gbs"], "unit": "GB/s", "peak_source": pk_src},

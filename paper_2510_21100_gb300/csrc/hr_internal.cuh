@@ -143,7 +143,7 @@ constexpr int kTileH = 32;
 inline int tiles_of(int W, int H) { return ((W + kTileW - 1) / kTileW) * ((H + kTileH - 1) / kTileH); }
 // Units of the 8-bit histogram pass: strips kStripW pixels wide and kBandH rows high, one warp each.
 constexpr int kStripW = 512;
-constexpr int kBandH = 8;
+constexpr int kBandH = 4;
 inline int strips_of(int W, int H) { return ((W + kStripW - 1) / kStripW) * ((H + kBandH - 1) / kBandH); }
 inline int interior_strips_of(int W, int H) { return (W / kStripW) * (H / kBandH); }
 

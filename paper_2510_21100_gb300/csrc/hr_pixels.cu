@@ -213,7 +213,7 @@ constexpr int kHT = kHW * 32;
 #define HR_STRIP_MIN_FACTOR 2  // strips per warp from which one image takes the strip kernel
 #endif
 constexpr int kHBins = 256;     // per-warp histogram stride (the 8-bit pass has K <= 256)
-constexpr int kRing = 4;        // rows in flight per lane
+constexpr int kRing = 3;        // rows in flight per warp (3 measured faster than 4 with 4-row bands)
 constexpr int kSlot = 32 * 48;  // bytes of one ring slot of a warp: 48 per lane
 
 // Shared memory of the fast histogram pass: per warp its two histograms, then per warp a ring
@@ -234,6 +234,7 @@ struct LaneTile {
   int x0, xc, cnt;      // tile origin column, first column of the lane, W - xc
   int lx;
   unsigned char* ring;  // the lane's 48 bytes in slot 0 (slot s at + s * kSlot)
+  unsigned char* slot0; // the warp's slot 0
   unsigned* nbr;        // the lane's neighbour word in slot 0 (slot s at + s * 32)
 };
 
@@ -259,24 +260,25 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // Starts the copies of row y into ring slot `slot` (one commit group per call; empty when
-// `live` is false): the lane's 48 bytes (a lane holding the image's last 1..15 pixels reads only
-// the row's own bytes and gets zeros after them), and the 4-byte neighbour word of lanes 0 and
-// 31.  Only the lane itself reads what it copied, so its own wait_group orders copies and reads.
+// `live` is false): the strip's 1536 bytes of the row as 96 chunks of 16 bytes, chunk c by lane
+// c mod 32, so each copy instruction of the warp covers 512 contiguous bytes (the bytes past the
+// image's last pixel are zero-filled), and the 4-byte neighbour words of lanes 0 and 31.  Lanes
+// read chunks other lanes copied: a __syncwarp after the wait_group orders copies and reads, one
+// before the next copies into a slot orders the reads before them.
 __device__ __forceinline__ void issue_row(const LaneTile& g, int slot, int y, bool live) {
   if (live) {
     const uint8_t* row = row_ptr(g, y);
-    unsigned char* dst = g.ring + slot * kSlot;
-    const uint8_t* src = row + 3 * g.xc;
-    if (g.cnt >= 16) {
-      cp_async16(dst, src);
-      cp_async16(dst + 16, src + 16);
-      cp_async16(dst + 32, src + 32);
-    } else if (g.cnt > 0) {
-      const int nb = 3 * g.cnt;  // 3 .. 45 bytes of the row remain
+    unsigned char* dst = g.slot0 + slot * kSlot;
+    const int b0 = 3 * g.x0, rowbytes = 3 * g.W;
+    if (b0 + kSlot <= rowbytes) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) cp_async16(dst + 16 * (g.lx + 32 * i), row + b0 + 16 * (g.lx + 32 * i));
+    } else {
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const int b = min(max(nb - 16 * i, 0), 16);
-        cp_async16z(dst + 16 * i, b > 0 ? (const void*)(src + 16 * i) : (const void*)row, b);
+        const int off = 16 * (g.lx + 32 * i);
+        const int b = min(max(rowbytes - (b0 + off), 0), 16);
+        cp_async16z(dst + off, b > 0 ? (const void*)(row + b0 + off) : (const void*)row, b);
       }
     }
     if (g.lx == 0 && g.x0 > 0) cp_async4(g.nbr + slot * 32, row + 3 * g.x0 - 4);
@@ -427,26 +429,33 @@ __device__ __forceinline__ void count_row(const VRow& T, const VRow& M, const VR
   }
 }
 
-// One tile for one lane; returns whether a level above K - 1 was seen.  Rows yb .. yb + 9 go
-// through the lane's ring, kRing rows ahead of use.
+// One strip for one lane; returns whether a level above K - 1 was seen.  Rows yb .. yb + kBandH + 1
+// go through the warp's ring, kRing rows ahead of use.
 template <bool kEdge, bool kClamp>
 __device__ __forceinline__ bool hist_tile(const LaneTile& g, int yb, int mclip, unsigned kk, unsigned hs_sh,
                                           unsigned hg_adj) {
   constexpr int kRows = kBandH + 2;
   bool bad = false;
+  __syncwarp();  // (the previous tile's reads of the ring are done)
 #pragma unroll
   for (int r = 0; r < kRing; ++r) issue_row(g, r, yb + r, true);
   cp_async_wait<kRing - 1>();
+  __syncwarp();
   VRow v0 = build_row<kEdge, kClamp>(g, 0, yb, kk, bad);
+  __syncwarp();
   issue_row(g, 0, yb + kRing, kRing < kRows);
   cp_async_wait<kRing - 1>();
+  __syncwarp();
   VRow v1 = build_row<kEdge, kClamp>(g, 1, yb + 1, kk, bad);
+  __syncwarp();
   issue_row(g, 1, yb + kRing + 1, kRing + 1 < kRows);
   const int full = kEdge ? min(g.cnt, 16) : 16;
 #pragma unroll
   for (int j = 0; j < kBandH; ++j) {
     cp_async_wait<kRing - 1>();
+    __syncwarp();
     const VRow v2 = build_row<kEdge, kClamp>(g, (j + 2) % kRing, yb + j + 2, kk, bad);
+    __syncwarp();
     issue_row(g, (j + 2) % kRing, yb + j + 2 + kRing, j + 2 + kRing < kRows);
     const int lim = kEdge ? (yb + j + 1 < g.H ? full : 0) : 16;
     count_row(v0, v1, v2, lim, mclip, hs_sh, hg_adj);
@@ -493,7 +502,8 @@ __global__ void __launch_bounds__(kHT, 1) hist_u8r_kernel(const ImgTab tab, int 
   const unsigned kk = 0x00010001u * (unsigned)(K - 1);
   LaneTile g;
   g.lx = lane;
-  g.ring = ring + (size_t)warp * kRing * kSlot + 48 * lane;
+  g.slot0 = ring + (size_t)warp * kRing * kSlot;
+  g.ring = g.slot0 + 48 * lane;
   g.nbr = nbr + warp * kRing * 32 + lane;
   int cur = -1;
   bool bad = false;

@@ -190,14 +190,14 @@ def test_batch_result_independent_of_batch_composition(hr):
 
 
 def test_large_batch_takes_strip_histograms(hr):
-    """A batch with enough 512 x 8 strips for the strip histogram kernel, which takes each image's
+    """A batch with enough 512 x 4 strips for the strip histogram kernel, which takes each image's
     interior strips first and then its right column and bottom band: every image gets the
     histograms, LUT and pixels it gets alone, and a few are checked against the oracle."""
     import torch
     from gpu_util import assert_close
     ctx, po = ctx_for(hr)
     sizes = [(1500, 1000), (1283, 725), (700, 333), (512, 480), (1024, 769), (95, 33), (1, 1), (2047, 1031)] * 4
-    assert sum(-(-w // 512) * -(-h // 8) for w, h in sizes) >= 2 * 152 * 16
+    assert sum(-(-w // 512) * -(-h // 4) for w, h in sizes) >= 2 * 152 * 16
     imgs = [synth.low_light_image(w, h, seed=5100 + i) for i, (w, h) in enumerate(sizes)]
     dins = [hr.to_device_aligned(im) for im in imgs]
     douts = [hr.aligned_empty(h, w) for (w, h) in sizes]
@@ -239,9 +239,9 @@ def _strip_pad(W):
 
 
 def test_large_ragged_image(hr):
-    """A single image large enough for the strip histogram kernel (one warp per 512 x 8 strip),
+    """A single image large enough for the strip histogram kernel (one warp per 512 x 4 strip),
     with a partial last strip (7001 = 13 * 512 + 345: a lane holding 9 pixels) and a partial last
-    band (4001 = 500 * 8 + 1)."""
+    band (4001 = 1000 * 4 + 1)."""
     ctx, po = ctx_for(hr)
     img = synth.low_light_image(7001, 4001, seed=synth.seed_for(1, 7))
     out, dbg = run_gpu(ctx, img, pad_elems=_strip_pad(7001))
