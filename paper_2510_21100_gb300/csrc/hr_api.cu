@@ -257,8 +257,8 @@ cudaError_t enqueue_stages(hr_ctx* c, const ImgTab& tab, int total, int units, i
   e = hr::launch_solve(a, n, C, st, (pdl & 2) != 0);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
-  e = hr::launch_apply(tab, total, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay, c->d_status,
-                       c->sm_count * c->tune.apply_ctas_per_sm, st, fast_out, (pdl & 4) != 0);
+  e = hr::launch_apply(tab, total, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay, c->d_status, c->sm_count,
+                       c->tune.apply_ctas_per_sm, st, fast_out, (pdl & 4) != 0);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return e;
   return cudaSuccess;

@@ -132,9 +132,9 @@ cudaError_t launch_hist(const ImgTab& tab, int total_tiles, int total_units, int
                         size_t slot_bytes, SlotLayout lay, unsigned* status, int sms, int ctas_per_sm,
                         cudaStream_t st, bool fast, bool pdl);
 cudaError_t launch_solve(const SolveArgs& a, int n, int cluster, cudaStream_t st, bool pdl);
-cudaError_t launch_apply(const ImgTab& tab, int total_tiles, int elem_bytes,
-                         int K, uint8_t* slots, size_t slot_bytes, SlotLayout lay, unsigned* status, int grid,
-                         cudaStream_t st, bool fast, bool pdl);
+cudaError_t launch_apply(const ImgTab& tab, int total_tiles, int elem_bytes, int K, uint8_t* slots, size_t slot_bytes,
+                         SlotLayout lay, unsigned* status, int sms, int ctas_per_sm, cudaStream_t st, bool fast,
+                         bool pdl);
 size_t solve_smem_bytes(int K, int vec_in_smem, int list_in_smem, size_t fsize);
 
 // Geometry of the pixel passes: tiles of kTileW x kTileH pixels.

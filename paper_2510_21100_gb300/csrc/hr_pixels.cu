@@ -887,10 +887,10 @@ cudaError_t launch_hist(const ImgTab& tab, int total_tiles, int total_units, int
 }
 
 cudaError_t launch_apply(const ImgTab& tab, int total_tiles, int elem_bytes, int K, uint8_t* slots, size_t slot_bytes,
-                         SlotLayout lay, unsigned* status, int grid, cudaStream_t st, bool fast, bool pdl) {
+                         SlotLayout lay, unsigned* status, int sms, int ctas_per_sm, cudaStream_t st, bool fast,
+                         bool pdl) {
   const size_t smem = (size_t)((K * 2 + 15) & ~15) + (size_t)K * sizeof(float);
-  if (grid > total_tiles) grid = total_tiles;
-  if (grid < 1) grid = 1;
+  const int grid = max(1, min(sms * ctas_per_sm, total_tiles));
   if (elem_bytes == 1 && fast)
     return launch_kernel(apply_u8v_kernel, dim3(grid), dim3(kThreads), 0, st, pdl, tab, total_tiles, K, slots,
                          slot_bytes, lay, status);
