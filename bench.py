@@ -233,8 +233,25 @@ def precision_leg(torch, hr, local, n_imgs=1024, steps=2, warmup=1):
     ms = e0.elapsed_time(e1) / steps
     mp = 1000 * 664 * n_imgs / 1e6
     ctx.close()
+    # accuracy of the FP32 form against the FP64 form (which the GPU tests hold to the FP64 oracle
+    # within 1e-9): max relative error of the enhanced histogram (per bin, relative to max(T, 1)) and
+    # LUT entries that differ, on four of the images
+    import numpy as np
+    errs, mism = [], 0
+    c32 = hr.Context(hr.Params(K=4096, precision=hr.PREC_FP32, debug=True), device=local)
+    c64 = hr.Context(hr.Params(K=4096, debug=True), device=local)
+    for im in pool[:4]:
+        c32.enhance(im)
+        c64.enhance(im)
+        d32, d64 = c32.debug(0), c64.debug(0)
+        errs.append(float(np.max(np.abs(d32["T"] - d64["T"]) / np.maximum(d64["T"], 1.0))))
+        mism += int(np.count_nonzero(d32["lut"] != d64["lut"]))
+    c32.close()
+    c64.close()
     return {"workload": f"{n_imgs} x 1000x664 uint16 (12-bit) images, K=4096, FP32 solve", "images": n_imgs,
-            "ms_per_batch": ms, "MP_per_s": mp / (ms / 1e3)}
+            "ms_per_batch": ms, "MP_per_s": mp / (ms / 1e3),
+            "accuracy_vs_fp64_form": {"images": 4, "max_rel_err_T": max(errs), "lut_entries_differing": mism,
+                                      "lut_entries": 4 * 4096}}
 
 
 def serving_leg(torch, hr, local, big_img, seconds=5.0, rate=400.0, seed=5):

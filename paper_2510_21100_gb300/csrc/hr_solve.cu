@@ -320,6 +320,7 @@ struct ClassPlan {
   uint2* piecep;       // own pieces, indexed by (piece - pA)
   void* partp;         // own piece sums (solver arithmetic type), indexed by (piece - pbase)
   unsigned pbase;      // pA for shared-memory buffers, 0 for the global workspace
+  bool glob;           // the lists are in the global workspace
 };
 
 // Own cell list, pieces and piece sums: shared-memory buffers when they fit, else the global
@@ -370,6 +371,7 @@ __device__ ClassPlan plan_classes(const cg::cluster_group& cl, int nR, int ncls,
     P.cell0 = 0;
   }
   P.pbase = (P.listp == ob.s_list) ? P.pA : 0u;
+  P.glob = P.listp != ob.s_list;
   const unsigned pbase = P.pbase;
   for (int c = P.cA + w; c < P.cB; c += NW) {  // own cells: warp per class, lanes over rows
     if (csz[c] == 0) continue;
@@ -408,19 +410,48 @@ __device__ void class_totals(const ClassPlan& P, const unsigned* csz, const unsi
                              EMIT emit) {
   F* part = static_cast<F*>(P.partp);
   const unsigned pbase = P.pbase;
-  for (unsigned p = P.pA + threadIdx.x; p < P.pB; p += NT) {
-    const uint2 pc = P.piecep[p - pbase];
-    const unsigned len = pc.y & 0xffffu;
-    const unsigned* cells = P.listp + pc.x;
-    F acc = 0;
+  // Lists in the global workspace (large K) are read at the latency of global memory: the FP32
+  // form keeps kU pieces per thread in flight (descriptors, then all their cells, then the sums).
+  constexpr int kU = std::is_same<F, float>::value ? 4 : 1;
+  if (kU > 1 && P.glob) {
+    for (unsigned p0 = P.pA + threadIdx.x; p0 < P.pB; p0 += kU * NT) {
+      uint2 pc[kU];
 #pragma unroll
-    for (unsigned c = 0; c < (unsigned)kPiece; ++c) {  // (all gathers of a piece in flight together)
-      if (c < len) {
-        const unsigned cell = cells[c];
-        acc = fmaF(Rc[cell >> 16], Lc[cell & 0xffffu], acc);
+      for (int u = 0; u < kU; ++u) {
+        const unsigned p = p0 + u * NT;
+        pc[u] = p < P.pB ? P.piecep[p - pbase] : make_uint2(0u, 0u);
+      }
+      unsigned cl[kU][kPiece];
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+#pragma unroll
+        for (unsigned c = 0; c < (unsigned)kPiece; ++c) cl[u][c] = c < (pc[u].y & 0xffffu) ? P.listp[pc[u].x + c] : 0u;
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const unsigned len = pc[u].y & 0xffffu;
+        F acc = 0;
+#pragma unroll
+        for (unsigned c = 0; c < (unsigned)kPiece; ++c)
+          if (c < len) acc = fmaF(Rc[cl[u][c] >> 16], Lc[cl[u][c] & 0xffffu], acc);
+        const unsigned p = p0 + u * NT;
+        if (p < P.pB) part[p - pbase] = acc;
       }
     }
-    part[p - pbase] = acc;
+  } else {
+    for (unsigned p = P.pA + threadIdx.x; p < P.pB; p += NT) {
+      const uint2 pc = P.piecep[p - pbase];
+      const unsigned len = pc.y & 0xffffu;
+      const unsigned* cells = P.listp + pc.x;
+      F acc = 0;
+#pragma unroll
+      for (unsigned c = 0; c < (unsigned)kPiece; ++c) {  // (all gathers of a piece in flight together)
+        if (c < len) {
+          const unsigned cell = cells[c];
+          acc = fmaF(Rc[cell >> 16], Lc[cell & 0xffffu], acc);
+        }
+      }
+      part[p - pbase] = acc;
+    }
   }
   __syncthreads();
   constexpr unsigned kSmall = 4;
