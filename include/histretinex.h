@@ -98,13 +98,17 @@ typedef struct hr_ctx hr_ctx;
  * histogram pass, bit 1 the solve, bit 2 the apply pass; 0..7): such a kernel is scheduled while
  * the kernel before it on the stream finishes and waits on the device for that kernel's results
  * (default 5, the two pixel passes; 0: plain stream order).  A dependent solve measured slower on
- * GB300 (its cluster is placed while the histogram pass drains). */
+ * GB300 (its cluster is placed while the histogram pass drains).  groups: a graph-replayed batch
+ * of at least 64 images runs as 1 or 2 groups (default 2: images [0, n/2) and [n/2, n) on two
+ * streams, the second group's histogram pass after the first's, so one group's solve overlaps the
+ * other's pixel passes). */
 typedef struct {
   int hist_ctas_per_sm;
   int apply_ctas_per_sm;
   int solve_cluster;
   int use_graph;
   int pdl;
+  int groups;
 } hr_tuning;
 
 /* Fills *p with the defaults: K = 256, alpha = beta = 1e-3, gamma = 2.2 (Sec. III.C),

@@ -49,6 +49,7 @@ class hr_tuning(ctypes.Structure):
         ("solve_cluster", ctypes.c_int),
         ("use_graph", ctypes.c_int),
         ("pdl", ctypes.c_int),
+        ("groups", ctypes.c_int),
     ]
 
 

@@ -18,6 +18,7 @@ CANDIDATES = {
     "apply_ctas_per_sm": (4, 8, 16),
     "solve_cluster": (4, 8, 16),
     "pdl": (0, 1, 5),  # dependent launches: none, histogram pass, histogram and apply passes
+    "groups": (1, 2),  # a large batch as one group or two overlapping ones
 }
 
 
@@ -61,7 +62,7 @@ def autotune(ctx, ins, outs=None, reps: int = 5, cache_path: str | None = DEFAUL
         return cache[key]["tuning"], cache[key]["ms"]
     best = ctx.tuning()
     best_ms = _time(ctx, ins, outs, reps, torch)
-    fields = ["hist_ctas_per_sm", "apply_ctas_per_sm"] + (["solve_cluster"] if len(ins) == 1 else []) + ["pdl"]
+    fields = ["hist_ctas_per_sm", "apply_ctas_per_sm"] + (["solve_cluster"] if len(ins) == 1 else ["groups"]) + ["pdl"]
     for field in fields:
         for v in CANDIDATES[field]:
             if v == best[field]:

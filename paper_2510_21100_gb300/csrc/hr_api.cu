@@ -47,14 +47,15 @@ struct hr_ctx {
   int ev_next = 0;
   double stage_ms[3] = {0, 0, 0};
   int stage_calls = 0;
-  hr_tuning tune{8, 8, 16, 1, 5};
+  hr_tuning tune{8, 8, 16, 1, 5, 2};
   // leading slots whose H_C(S) and H_C(grad S) are known to be zero (the solve clears them after
   // use unless the intermediates are kept for histretinex_get_debug)
   int hist_clean = 0;
   // captured batch pipeline and the geometry it was captured for
   cudaGraphExec_t graph = nullptr;
-  int g_n = 0, g_total = 0, g_eb = 0, g_fast_in = 0, g_fast_out = 0, g_zero = 0;
-  hr_tuning g_tune{0, 0, 0, 0, 0};
+  int g_n = 0, g_total = 0, g_eb = 0, g_fast_in = 0, g_fast_out = 0, g_zero = 0, g_groups = 0;
+  hr_tuning g_tune{0, 0, 0, 0, 0, 0};
+  int last_groups = 0;  // groups of the uploaded tables
 };
 
 namespace hr {
@@ -178,10 +179,10 @@ hr_status ensure_desc(hr_ctx* c, int n) {
   c->d_imgs = nullptr; c->d_tile_start = nullptr; c->h_imgs = nullptr; c->h_tile_start = nullptr; c->cap_imgs = 0;
   c->last_imgs.clear();
   HR_CUDA(cudaMalloc(&c->d_imgs, sizeof(ImageDesc) * (size_t)n));
-  // tile starts, strip starts, then the solve's image order
-  HR_CUDA(cudaMalloc(&c->d_tile_start, sizeof(int) * 3 * (size_t)(n + 1)));
+  // per group of images (at most two): tile starts, strip starts, then the solve's image order
+  HR_CUDA(cudaMalloc(&c->d_tile_start, sizeof(int) * 3 * (size_t)(n + 2)));
   HR_CUDA(cudaMallocHost(&c->h_imgs, sizeof(ImageDesc) * (size_t)n));
-  HR_CUDA(cudaMallocHost(&c->h_tile_start, sizeof(int) * 3 * (size_t)(n + 1)));
+  HR_CUDA(cudaMallocHost(&c->h_tile_start, sizeof(int) * 3 * (size_t)(n + 2)));
   c->cap_imgs = n;
   return HR_OK;
 }
@@ -209,25 +210,34 @@ hr_status fold_timing(hr_ctx* c, int i) {
   return HR_OK;
 }
 
-// The pipeline's device work on one stream: zero the histograms (unless the previous solves left
-// them zero), histogram pass, solve, apply.  ev (optional): four events recorded around the three
-// stages.
-cudaError_t enqueue_stages(hr_ctx* c, const ImgTab& tab, int total, int units, int interior, int elem_bytes, bool fast_in,
-                           bool fast_out, bool batched, bool zero, cudaStream_t st, cudaEvent_t* ev) {
-  const int K = c->p.K, n = tab.n;
+// The images one enqueue_stages call runs: their table, work totals, first slot and solve order.
+struct Group {
+  ImgTab tab;
+  int total, units, interior;
+  uint8_t* slots;
+  const int* order;  // (nullptr for one image)
+};
+
+// The pipeline's device work for one group on one stream: zero the histograms (unless the previous
+// solves left them zero), histogram pass, solve, apply.  ev (optional): four events recorded around
+// the three stages; after_hist (optional): recorded after the histogram pass.
+cudaError_t enqueue_stages(hr_ctx* c, const Group& g, int elem_bytes, bool fast_in, bool fast_out, bool batched,
+                           bool zero, cudaStream_t st, cudaEvent_t* ev, cudaEvent_t after_hist = nullptr) {
+  const int K = c->p.K, n = g.tab.n;
   const int pdl = c->tune.pdl;  // bit 0: histogram pass, bit 1: solve, bit 2: apply pass
   const bool debug = (c->p.flags & HR_FLAG_DEBUG_OUT) != 0;
   cudaError_t e;
   // zero H_C(S) and H_C(grad S) of every slot used (S and G are adjacent at the slot start)
   if (zero) {
-    e = cudaMemset2DAsync(c->d_slots + c->lay.S, c->lay.bytes, 0, (size_t)2 * K * sizeof(unsigned), (size_t)n, st);
+    e = cudaMemset2DAsync(g.slots + c->lay.S, c->lay.bytes, 0, (size_t)2 * K * sizeof(unsigned), (size_t)n, st);
     if (e != cudaSuccess) return e;
   }
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-  e = hr::launch_hist(tab, total, units, interior, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay, c->d_status, c->sm_count,
-                      c->tune.hist_ctas_per_sm, st, fast_in, (pdl & 1) != 0);
+  e = hr::launch_hist(g.tab, g.total, g.units, g.interior, elem_bytes, K, g.slots, c->lay.bytes, c->lay, c->d_status,
+                      c->sm_count, c->tune.hist_ctas_per_sm, st, fast_in, (pdl & 1) != 0);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
+  if (after_hist && (e = cudaEventRecord(after_hist, st)) != cudaSuccess) return e;
   hr::SolveArgs a{};
   a.K = K;
   a.alpha = c->p.alpha;
@@ -236,8 +246,8 @@ cudaError_t enqueue_stages(hr_ctx* c, const ImgTab& tab, int total, int units, i
   a.max_iter = c->p.max_iter;
   a.fixed_iters = (c->p.flags & HR_FLAG_FIXED_ITERS) ? 1 : 0;
   a.jstart1 = c->d_jstart1;
-  a.slots = c->d_slots;
-  a.order = n > 1 ? c->d_tile_start + 2 * (n + 1) : nullptr;
+  a.slots = g.slots;
+  a.order = g.order;
   a.slot_bytes = c->lay.bytes;
   a.lay = c->lay;
   a.status = c->d_status;
@@ -257,7 +267,7 @@ cudaError_t enqueue_stages(hr_ctx* c, const ImgTab& tab, int total, int units, i
   e = hr::launch_solve(a, n, C, st, (pdl & 2) != 0);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
-  e = hr::launch_apply(tab, total, elem_bytes, K, c->d_slots, c->lay.bytes, c->lay, c->d_status, c->sm_count,
+  e = hr::launch_apply(g.tab, g.total, elem_bytes, K, g.slots, c->lay.bytes, c->lay, c->d_status, c->sm_count,
                        c->tune.apply_ctas_per_sm, st, fast_out, (pdl & 4) != 0);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return e;
@@ -275,7 +285,7 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
   const int K = c->p.K;
   if (elem_bytes != 1 && elem_bytes != 2) return HR_ERR_INVALID_ARG;
   if (elem_bytes == 1 && K > 256) return HR_ERR_INVALID_ARG;
-  long long total = 0, units = 0, interior = 0;
+  long long total = 0, units = 0;
   for (int i = 0; i < n; ++i) {
     const ImageDesc& d = imgs[i];
     if (!d.in || !d.out || d.W < 1 || d.H < 1) return HR_ERR_INVALID_ARG;
@@ -284,7 +294,6 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
     if ((long long)d.W * d.H >= (1LL << 31)) return HR_ERR_UNSUPPORTED;
     total += hr::tiles_of(d.W, d.H);
     units += hr::strips_of(d.W, d.H);
-    interior += hr::interior_strips_of(d.W, d.H);
   }
   if (total >= (1LL << 31) || units >= (1LL << 31)) return HR_ERR_UNSUPPORTED;
   // 8-bit fast paths need every row 16-byte aligned (input for the histogram pass, both for apply)
@@ -298,45 +307,70 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
   }
   hr_status s = ensure_slots(c, n);
   if (s != HR_OK) return s;
-  ImgTab tab{};
-  tab.n = n;
-  if (n == 1) {
-    tab.one = imgs[0];  // travels in the kernel parameters: nothing to upload
-  } else {
-    s = ensure_desc(c, n);
-    if (s != HR_OK) return s;
-    if (!same_desc(c->last_imgs, imgs, n)) {
-      HR_CUDA(cudaEventSynchronize(c->desc_done));  // the previous upload has left the staging buffer
-      int t = 0, u = 0;
-      for (int i = 0; i < n; ++i) {
-        c->h_imgs[i] = imgs[i];
-        c->h_tile_start[i] = t;
-        c->h_tile_start[n + 1 + i] = u;
-        t += hr::tiles_of(imgs[i].W, imgs[i].H);
-        u += hr::strips_of(imgs[i].W, imgs[i].H);
-      }
-      c->h_tile_start[n] = t;
-      c->h_tile_start[2 * n + 1] = u;
-      // the solve's CTAs take the images largest first (longest solves first: the last wave holds
-      // the shortest ones)
-      int* order = c->h_tile_start + 2 * (n + 1);
-      for (int i = 0; i < n; ++i) order[i] = i;
-      std::stable_sort(order, order + n, [&](int x, int y) {
-        return (long long)imgs[x].W * imgs[x].H > (long long)imgs[y].W * imgs[y].H;
-      });
-      HR_CUDA(cudaMemcpyAsync(c->d_imgs, c->h_imgs, sizeof(ImageDesc) * (size_t)n, cudaMemcpyHostToDevice, st));
-      HR_CUDA(cudaMemcpyAsync(c->d_tile_start, c->h_tile_start, sizeof(int) * 3 * (size_t)(n + 1),
-                              cudaMemcpyHostToDevice, st));
-      HR_CUDA(cudaEventRecord(c->desc_done, st));
-      c->last_imgs.assign(imgs, imgs + n);
-    }
-    tab.imgs = c->d_imgs;
-    tab.tiles = c->d_tile_start;
-    tab.units = c->d_tile_start + n + 1;
-  }
   const bool debug = (c->p.flags & HR_FLAG_DEBUG_OUT) != 0;
   const bool timing = (c->p.flags & HR_FLAG_STAGE_TIMING) != 0;
   const bool graph = batched && c->tune.use_graph && n > 1 && !timing;
+  // A large graph-replayed batch may run as two groups (images [0, n/2) and [n/2, n)) on two
+  // streams, the second group's histogram pass after the first's, so that one group's solve
+  // overlaps the other's pixel passes.
+  const int G = (graph && c->tune.groups == 2 && n >= 64) ? 2 : 1;
+  int g0[2] = {0, G == 2 ? n / 2 : n}, gn[2] = {G == 2 ? n / 2 : n, G == 2 ? n - n / 2 : 0};
+  Group grp[2] = {};
+  for (int g = 0; g < G; ++g) {
+    Group& q = grp[g];
+    q.tab.n = gn[g];
+    q.slots = c->d_slots + (size_t)g0[g] * c->lay.bytes;
+    for (int i = g0[g]; i < g0[g] + gn[g]; ++i) {
+      q.total += hr::tiles_of(imgs[i].W, imgs[i].H);
+      q.units += hr::strips_of(imgs[i].W, imgs[i].H);
+      q.interior += hr::interior_strips_of(imgs[i].W, imgs[i].H);
+    }
+    if (gn[g] == 1) q.tab.one = imgs[g0[g]];  // travels in the kernel parameters: nothing to upload
+  }
+  if (n > 1) {
+    s = ensure_desc(c, n);
+    if (s != HR_OK) return s;
+    if (!same_desc(c->last_imgs, imgs, n) || c->last_groups != G) {
+      HR_CUDA(cudaEventSynchronize(c->desc_done));  // the previous upload has left the staging buffer
+      for (int i = 0; i < n; ++i) c->h_imgs[i] = imgs[i];
+      for (int g = 0; g < G; ++g) {
+        const int m = gn[g], off = 3 * (g0[g] + g);
+        int* tiles = c->h_tile_start + off;
+        int* strips = tiles + m + 1;
+        int* order = tiles + 2 * (m + 1);
+        int t = 0, u = 0;
+        for (int i = 0; i < m; ++i) {
+          tiles[i] = t;
+          strips[i] = u;
+          t += hr::tiles_of(imgs[g0[g] + i].W, imgs[g0[g] + i].H);
+          u += hr::strips_of(imgs[g0[g] + i].W, imgs[g0[g] + i].H);
+        }
+        tiles[m] = t;
+        strips[m] = u;
+        // the solve's CTAs take the group's images largest first (longest solves first: the last
+        // wave holds the shortest ones)
+        for (int i = 0; i < m; ++i) order[i] = i;
+        std::stable_sort(order, order + m, [&](int x, int y) {
+          const ImageDesc &dx = imgs[g0[g] + x], &dy = imgs[g0[g] + y];
+          return (long long)dx.W * dx.H > (long long)dy.W * dy.H;
+        });
+      }
+      HR_CUDA(cudaMemcpyAsync(c->d_imgs, c->h_imgs, sizeof(ImageDesc) * (size_t)n, cudaMemcpyHostToDevice, st));
+      HR_CUDA(cudaMemcpyAsync(c->d_tile_start, c->h_tile_start, sizeof(int) * 3 * (size_t)(n + G),
+                              cudaMemcpyHostToDevice, st));
+      HR_CUDA(cudaEventRecord(c->desc_done, st));
+      c->last_imgs.assign(imgs, imgs + n);
+      c->last_groups = G;
+    }
+    for (int g = 0; g < G; ++g) {  // each group's tables: tile starts, strip starts, solve order
+      if (gn[g] == 1) continue;
+      const int off = 3 * (g0[g] + g);
+      grp[g].tab.imgs = c->d_imgs + g0[g];
+      grp[g].tab.tiles = c->d_tile_start + off;
+      grp[g].tab.units = grp[g].tab.tiles + gn[g] + 1;
+      grp[g].order = grp[g].tab.tiles + 2 * (gn[g] + 1);
+    }
+  }
   if (graph) {
     // a replayed graph cannot see whether the histograms are zero: without debug intermediates it
     // relies on the solves clearing them (cleared here first if need be), with them it zeroes
@@ -348,29 +382,52 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
     }
     const bool same = c->graph && c->g_n == n && c->g_total == (int)total && c->g_eb == elem_bytes &&
                       c->g_fast_in == (int)fast_in && c->g_fast_out == (int)fast_out && c->g_zero == (int)debug &&
-                      std::memcmp(&c->g_tune, &c->tune, sizeof(hr_tuning)) == 0;
+                      c->g_groups == G && std::memcmp(&c->g_tune, &c->tune, sizeof(hr_tuning)) == 0;
     if (!same) {
       drop_graph(c);
-      cudaStream_t cap;
+      cudaStream_t cap = nullptr, cap2 = nullptr;
+      cudaEvent_t fork = nullptr, hist_done = nullptr, join = nullptr;
       HR_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-      cudaGraph_t g = nullptr;
-      cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      cudaError_t e = cudaSuccess;
+      if (G == 2) {
+        e = cudaStreamCreateWithFlags(&cap2, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hist_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+      }
+      cudaGraph_t gr = nullptr;
+      if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        e = enqueue_stages(c, tab, (int)total, (int)units, (int)interior, elem_bytes, fast_in, fast_out, batched, debug, cap, nullptr);
-        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (G == 2) {
+          e = cudaEventRecord(fork, cap);
+          if (e == cudaSuccess) e = cudaStreamWaitEvent(cap2, fork, 0);
+        }
+        if (e == cudaSuccess)
+          e = enqueue_stages(c, grp[0], elem_bytes, fast_in, fast_out, batched, debug, cap, nullptr, hist_done);
+        if (G == 2) {
+          if (e == cudaSuccess) e = cudaStreamWaitEvent(cap2, hist_done, 0);
+          if (e == cudaSuccess) e = enqueue_stages(c, grp[1], elem_bytes, fast_in, fast_out, batched, debug, cap2, nullptr);
+          if (e == cudaSuccess) e = cudaEventRecord(join, cap2);
+          if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, join, 0);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cap, &gr);
         if (e == cudaSuccess) e = e2;
       }
-      if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);
-      if (g) cudaGraphDestroy(g);
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, gr, 0);
+      if (gr) cudaGraphDestroy(gr);
+      if (join) cudaEventDestroy(join);
+      if (hist_done) cudaEventDestroy(hist_done);
+      if (fork) cudaEventDestroy(fork);
+      if (cap2) cudaStreamDestroy(cap2);
       cudaStreamDestroy(cap);
       if (e != cudaSuccess) { c->graph = nullptr; return cuda_fail(e); }
-      c->g_n = n; c->g_total = (int)total; c->g_eb = elem_bytes;
+      c->g_n = n; c->g_total = (int)total; c->g_eb = elem_bytes; c->g_groups = G;
       c->g_fast_in = (int)fast_in; c->g_fast_out = (int)fast_out; c->g_zero = (int)debug; c->g_tune = c->tune;
     }
     const cudaError_t e = cudaGraphLaunch(c->graph, st);
     note_hist_state(c, n, e == cudaSuccess);
     if (e != cudaSuccess) return cuda_fail(e);
-    c->launches += 3;
+    c->launches += 3 * G;
     c->last_n = n;
     return HR_OK;
   }
@@ -386,7 +443,7 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
     c->ev_used[i] = true;
   }
   const bool zero = debug || c->hist_clean < n;
-  const cudaError_t e = enqueue_stages(c, tab, (int)total, (int)units, (int)interior, elem_bytes, fast_in, fast_out, batched, zero, st, ev);
+  const cudaError_t e = enqueue_stages(c, grp[0], elem_bytes, fast_in, fast_out, batched, zero, st, ev);
   note_hist_state(c, n, e == cudaSuccess);
   if (e != cudaSuccess) return cuda_fail(e);
   c->launches += 3;
@@ -688,6 +745,7 @@ hr_status histretinex_set_tuning(hr_ctx* c, const hr_tuning* t) {
     return HR_ERR_INVALID_ARG;
   if (t->use_graph != 0 && t->use_graph != 1) return HR_ERR_INVALID_ARG;
   if (t->pdl < 0 || t->pdl > 7) return HR_ERR_INVALID_ARG;
+  if (t->groups != 1 && t->groups != 2) return HR_ERR_INVALID_ARG;
   c->tune = *t;
   return HR_OK;
 }
