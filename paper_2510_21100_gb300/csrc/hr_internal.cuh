@@ -79,7 +79,7 @@ struct SlotLayout {
   size_t lut;           // uint16[K]
   size_t misc;          // int[4]: iterations, nR, nL, cells; then long long[kProfSlots] phase times
   size_t vec;           // solver vectors when they do not fit in shared memory
-  size_t cls;           // uint32[4*K]: class size, cell start, first piece, piece count
+  size_t cls;           // uint32[4*K]: spare
   size_t list;          // uint32[K*(K+1)]: class-major cell lists, (a << 16) | b; then the
                         // Eq. 19 row segments (at most K (K+1) / 2 solver values)
   size_t piece;         // uint2[max_pieces]: (cell start, len | class << 16)

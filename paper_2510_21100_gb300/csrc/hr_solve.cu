@@ -570,10 +570,11 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   // ---- Eq. 11 classes that matter (S_k > 0): plan and own cell lists -------------------------
   cl.sync();  // every CTA of the cluster has started before any distributed shared memory access
   stamp();
-  // per-row reciprocals of the Eq. 11 boundary division, in the LUT scan buffer (free until then)
+  // per-row reciprocals of the Eq. 11 boundary division, in the LUT scan buffer (free until then),
+  // for up to 512 rows (more rows: the FP32 quotient; a table in the workspace measured slower)
   unsigned long long* mg = nullptr;
-  if (nR <= NT) {
-    mg = reinterpret_cast<unsigned long long*>(scr);
+  if (nR <= NT) mg = reinterpret_cast<unsigned long long*>(scr);
+  if (mg) {
     for (int a = tid; a < nR; a += NT) mg[a] = RI[a] ? ~0ull / (2ull * RI[a]) + 1ull : 0ull;
     __syncthreads();
   }
@@ -783,9 +784,9 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   unsigned* rk0 = csz;   // per own row: first class (the class-plan arrays are free by now)
   unsigned* rk1 = cst;   // per own row: last class
   // Where the row pass puts its sums, in the shared memory the cell lists used (free now) when
-  // they fit, else in the workspace: a few own rows (cluster CTAs) each get a segment; many (a CTA
-  // alone) add into per-warp partial targets instead (a warp's rows in order, then the warps in
-  // order), which spares the pass over all rows per class.
+  // they fit, else in the workspace (the cell-list area): a few own rows (cluster CTAs) each get a
+  // segment; many (a CTA alone) add into per-warp partial targets instead (a warp's rows in order,
+  // then the warps in order), which spares the pass over all rows per class.
   const size_t room = (size_t)kPieceCap * (sizeof(F) + sizeof(uint2)) + (size_t)kListCap * sizeof(unsigned);
   const bool few_rows = aB - aA <= 32;
   F* seg_s = nullptr;
@@ -794,6 +795,8 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     if (few_rows && (size_t)(aB - aA) * K * sizeof(F) <= room) seg_s = static_cast<F*>(ob.s_part);
     if (!few_rows && (size_t)NW * K * sizeof(F) <= room) wacc = static_cast<F*>(ob.s_part);
   }
+  if (!few_rows && !wacc && (size_t)C * NW * K * sizeof(F) <= (size_t)K * (K + 1) * 4)
+    wacc = reinterpret_cast<F*>(slot + lay.list) + (size_t)rank * NW * K;  // (large K: a block per CTA)
   if (wacc) {
     for (int e = tid; e < NW * K; e += NT) wacc[e] = (F)0.0;
     __syncthreads();
@@ -837,6 +840,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
           else out[k] = r * sum;
         }
       }
+      __syncwarp();  // (the next row's additions may come from other lanes)
     }
   }
   __syncthreads();
@@ -845,20 +849,9 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     F sum = 0.0;
     if (wacc) {
       for (int w = 0; w < NW; ++w) sum += wacc[w * K + k];
-    } else if (few_rows) {  // a branch per row: whole warps skip the rows that miss their classes
+    } else {  // a few rows, a branch per row: whole warps skip the rows that miss their classes
       for (int a = aA; a < aB; ++a)
         if ((int)rk0[a] <= k && k <= (int)rk1[a]) sum += seg_of(a)[k];
-    } else {  // eight rows' loads in flight together, rows ascending
-      for (int a0 = aA; a0 < aB; a0 += 8) {
-        F v[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int a = a0 + t;
-          v[t] = (a < aB && (int)rk0[a] <= k && k <= (int)rk1[a]) ? seg_of(a)[k] : (F)0.0;
-        }
-#pragma unroll
-        for (int t = 0; t < 8; ++t) sum += v[t];
-      }
     }
     Tp[k] = sum;
   }
