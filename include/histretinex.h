@@ -87,8 +87,9 @@ typedef struct {
 typedef struct hr_ctx hr_ctx;
 
 /* Launch shapes (not part of the paper's method).  hist_ctas_per_sm, apply_ctas_per_sm: the
- * persistent grids of the two pixel passes are SMs x this many CTAs (1..32; default 8; the 8-bit
- * histogram kernel for one large image with 16-byte aligned rows runs one CTA per SM instead);
+ * persistent grids of the two pixel passes are SMs x this many CTAs (1..32; defaults 8 and 16; the
+ * 8-bit strip histogram kernel for large images and batches with 16-byte aligned rows runs one CTA
+ * per SM instead);
  * solve_cluster: CTAs per thread-block cluster of an image's solve (1, 2, 4, 8 or 16; default 16,
  * lowered automatically when that cluster cannot be resident; a batch of n images uses at most
  * SMs / n, rounded down to a power of two, so that it runs in one wave); use_graph: 1 to

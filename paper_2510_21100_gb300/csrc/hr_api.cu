@@ -47,7 +47,7 @@ struct hr_ctx {
   int ev_next = 0;
   double stage_ms[3] = {0, 0, 0};
   int stage_calls = 0;
-  hr_tuning tune{8, 8, 16, 1, 5, 2};
+  hr_tuning tune{8, 16, 16, 1, 5, 2};
   // leading slots whose H_C(S) and H_C(grad S) are known to be zero (the solve clears them after
   // use unless the intermediates are kept for histretinex_get_debug)
   int hist_clean = 0;

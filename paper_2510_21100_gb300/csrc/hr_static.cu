@@ -115,6 +115,6 @@ extern "C" hr_status histretinex_enhance_noalloc(const hr_params* p, const void*
   a.arith = p->precision == HR_PREC_FP32 ? hr::kArithF32 : (p->precision == HR_PREC_DF64 ? hr::kArithDF64 : hr::kArithF64);
   e = hr::launch_solve(a, 1, 16, st, false);
   if (e != cudaSuccess) return HR_ERR_CUDA;
-  e = hr::launch_apply(tab, tiles, elem_bytes, K, base, lay.bytes, lay, d_status, sms, 8, st, fast_out, true);
+  e = hr::launch_apply(tab, tiles, elem_bytes, K, base, lay.bytes, lay, d_status, sms, 16, st, fast_out, true);
   return e == cudaSuccess ? HR_OK : HR_ERR_CUDA;
 }
