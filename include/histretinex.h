@@ -48,7 +48,7 @@ extern "C" {
 typedef enum {
   HR_OK = 0,
   HR_ERR_INVALID_ARG = 1,  /* a bad pointer, size, pitch or parameter */
-  HR_ERR_UNSUPPORTED = 2,  /* a valid request this build does not handle (see each call) */
+  HR_ERR_UNSUPPORTED = 2,  /* a valid request the library does not handle (see each call) */
   HR_ERR_OOM = 3,          /* device or host allocation failed */
   HR_ERR_CUDA = 4,         /* a CUDA runtime call failed */
   HR_ERR_RANGE = 5,        /* an image held a level >= K */
