@@ -53,7 +53,7 @@ struct hr_ctx {
   int hist_clean = 0;
   // captured batch pipeline and the geometry it was captured for
   cudaGraphExec_t graph = nullptr;
-  int g_n = 0, g_total = 0, g_eb = 0, g_fast_in = 0, g_fast_out = 0, g_zero = 0, g_groups = 0;
+  int g_n = 0, g_total = 0, g_eb = 0, g_fast_in = 0, g_fast_out = 0, g_zero = 0, g_groups = 0, g_launches = 0;
   hr_tuning g_tune{0, 0, 0, 0, 0, 0};
   int last_groups = 0;  // groups of the uploaded tables
 };
@@ -222,7 +222,8 @@ struct Group {
 // solves left them zero), histogram pass, solve, apply.  ev (optional): four events recorded around
 // the three stages; after_hist (optional): recorded after the histogram pass.
 cudaError_t enqueue_stages(hr_ctx* c, const Group& g, int elem_bytes, bool fast_in, bool fast_out, bool batched,
-                           bool zero, cudaStream_t st, cudaEvent_t* ev, cudaEvent_t after_hist = nullptr) {
+                           bool zero, cudaStream_t st, cudaEvent_t* ev, int* launches,
+                           cudaEvent_t after_hist = nullptr) {
   const int K = c->p.K, n = g.tab.n;
   const int pdl = c->tune.pdl;  // bit 0: histogram pass, bit 1: solve, bit 2: apply pass
   const bool debug = (c->p.flags & HR_FLAG_DEBUG_OUT) != 0;
@@ -257,6 +258,7 @@ cudaError_t enqueue_stages(hr_ctx* c, const Group& g, int elem_bytes, bool fast_
   // CTAs per image: the tuned cluster for one image; for a batch as many as keep all images in
   // one wave (the largest power of two with n C <= SMs, at most the tuned cluster), so a batch
   // of a few images runs as fast as its images would alone and a large one on one CTA each
+  *launches += 3;
   int C = c->tune.solve_cluster;
   if (batched) {
     const int per = c->sm_count / n;
@@ -396,6 +398,7 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
       }
       cudaGraph_t gr = nullptr;
+      int nl = 0;  // kernels per replay
       if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
         if (G == 2) {
@@ -403,10 +406,11 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
           if (e == cudaSuccess) e = cudaStreamWaitEvent(cap2, fork, 0);
         }
         if (e == cudaSuccess)
-          e = enqueue_stages(c, grp[0], elem_bytes, fast_in, fast_out, batched, debug, cap, nullptr, hist_done);
+          e = enqueue_stages(c, grp[0], elem_bytes, fast_in, fast_out, batched, debug, cap, nullptr, &nl, hist_done);
         if (G == 2) {
           if (e == cudaSuccess) e = cudaStreamWaitEvent(cap2, hist_done, 0);
-          if (e == cudaSuccess) e = enqueue_stages(c, grp[1], elem_bytes, fast_in, fast_out, batched, debug, cap2, nullptr);
+          if (e == cudaSuccess)
+            e = enqueue_stages(c, grp[1], elem_bytes, fast_in, fast_out, batched, debug, cap2, nullptr, &nl);
           if (e == cudaSuccess) e = cudaEventRecord(join, cap2);
           if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, join, 0);
         }
@@ -421,13 +425,13 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
       if (cap2) cudaStreamDestroy(cap2);
       cudaStreamDestroy(cap);
       if (e != cudaSuccess) { c->graph = nullptr; return cuda_fail(e); }
-      c->g_n = n; c->g_total = (int)total; c->g_eb = elem_bytes; c->g_groups = G;
+      c->g_n = n; c->g_total = (int)total; c->g_eb = elem_bytes; c->g_groups = G; c->g_launches = nl;
       c->g_fast_in = (int)fast_in; c->g_fast_out = (int)fast_out; c->g_zero = (int)debug; c->g_tune = c->tune;
     }
     const cudaError_t e = cudaGraphLaunch(c->graph, st);
     note_hist_state(c, n, e == cudaSuccess);
     if (e != cudaSuccess) return cuda_fail(e);
-    c->launches += 3 * G;
+    c->launches += (uint64_t)c->g_launches;
     c->last_n = n;
     return HR_OK;
   }
@@ -443,10 +447,11 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
     c->ev_used[i] = true;
   }
   const bool zero = debug || c->hist_clean < n;
-  const cudaError_t e = enqueue_stages(c, grp[0], elem_bytes, fast_in, fast_out, batched, zero, st, ev);
+  int nl = 0;
+  const cudaError_t e = enqueue_stages(c, grp[0], elem_bytes, fast_in, fast_out, batched, zero, st, ev, &nl);
   note_hist_state(c, n, e == cudaSuccess);
   if (e != cudaSuccess) return cuda_fail(e);
-  c->launches += 3;
+  c->launches += (uint64_t)nl;
   c->last_n = n;
   return HR_OK;
 }
