@@ -28,7 +28,7 @@ UNIT = "MP/s"
 # DRAM bytes (read + write) per launch of each kernel at 7680x4320, K = 256, from one ncu capture
 # of the current kernels (profiles/*_7680x4320.md); the apply's writes still in L2 when the
 # kernel ends are not counted there.
-PROFILED_DRAM_BYTES = {"hist_u8r_kernel": 108_050_176, "solve_kernel<double>": 210_432, "apply_u8v_kernel": 147_478_272}
+PROFILED_DRAM_BYTES = {"hist_u8r_kernel": 107_502_592, "solve_kernel<double>": 210_688, "apply_u8v_kernel": 147_325_440}
 
 
 def parse():
