@@ -154,6 +154,32 @@ def test_batch_equals_single_images(hr):
         compare_to_oracle(im, out_b, batch_dbg[i], po)
 
 
+def test_batch_of_large_images_takes_both_strip_paths(hr):
+    """Two large images in one batch (few edge strips: each image's interior strips on the interior
+    path, its edge strips on the edge path): histograms, LUT and pixels as each image gets alone
+    (there on the staged tiles, 4096 strips being below the strip kernel's threshold)."""
+    import torch
+    from gpu_util import assert_close
+    ctx, po = ctx_for(hr)
+    sizes = [(4096, 2048), (4000, 2001)]
+    assert sum(-(-w // 512) * -(-h // 4) for w, h in sizes) >= 2 * 152 * 16
+    imgs = [synth.low_light_image(w, h, seed=5300 + i) for i, (w, h) in enumerate(sizes)]
+    dins = [hr.to_device_aligned(im) for im in imgs]
+    douts = [hr.aligned_empty(h, w) for (w, h) in sizes]
+    ctx.enhance_batch(dins, douts)
+    ctx.check()
+    batch = [(douts[i].cpu().numpy(), ctx.debug(i)) for i in range(len(imgs))]
+    for i, im in enumerate(imgs):
+        out_b, dbg_b = batch[i]
+        out_s, dbg_s = run_gpu(ctx, im)
+        for k in ("S", "G", "lut"):
+            assert np.array_equal(dbg_b[k], dbg_s[k]), (i, k)
+        for k in ("R", "L", "T"):
+            assert_close(dbg_b[k], dbg_s[k], k)
+        assert np.array_equal(out_b, out_s), i
+    compare_to_oracle(imgs[1], batch[1][0], batch[1][1], po)
+
+
 def test_batch_of_one_is_the_single_image_call(hr):
     """A batch of one image runs the single-image pipeline's kernels with the same cluster: the
     same bits throughout."""
