@@ -217,7 +217,8 @@ constexpr int kRing = 3;        // rows in flight per warp (3 measured faster th
 constexpr int kSlot = 32 * 48;  // bytes of one ring slot of a warp: 48 per lane
 
 // Shared memory of the fast histogram pass: per warp its two histograms, then per warp a ring
-// of kRing row slots (48 bytes per lane each) and of kRing neighbour words per lane.
+// of kRing row slots (the strip's 1536 bytes of a row: 48 bytes per lane) and of kRing neighbour
+// words per lane.
 constexpr size_t kHistSmem = (size_t)kHW * (4 * kHBins * 4 + kRing * kSlot + kRing * 32 * 4);
 
 // One row of V around a lane's 16 pixels.
@@ -226,12 +227,12 @@ struct VRow {
   unsigned l, r;        // high half of l: V of the pixel left of the 16; low half of r: the one right
 };
 
-// Per-lane geometry of the current tile and the lane's ring slots.
+// Per-lane geometry of the current strip and the lane's view of the warp's ring.
 struct LaneTile {
   const uint8_t* in;
   long long pitch;
   int W, H;
-  int x0, xc, cnt;      // tile origin column, first column of the lane, W - xc
+  int x0, xc, cnt;      // strip origin column, first column of the lane, W - xc
   int lx;
   unsigned char* ring;  // the lane's 48 bytes in slot 0 (slot s at + s * kSlot)
   unsigned char* slot0; // the warp's slot 0

@@ -600,11 +600,11 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   // instruction holds its SM sub-partition's FP64 pipe for about 64 cycles however many lanes are
   // active, while one lane's sum is a chain of dependent steps, so for a cluster CTA the choice
   // minimises the larger of the busiest sub-partition's FP64 cycles, ceil(warps / 4) x (terms per
-  // lane + shuffle-tree levels) x 64, and a lane's chain.  A CTA alone (batches: one image per CTA,
-  // many rows each) uses 4.  (One image's arithmetic depends on C only
-  // through these group sizes and the class split.)
-  // unrolling the Eq. 12/13 sums pays for the double-float form (FP32 pipes) and costs the FP64
-  // form more than it gains (measured on GB300: -3.7 us per 8K image without it)
+  // lane + shuffle-tree levels) x 64, and a lane's chain.  A CTA alone (large batches: one image per
+  // CTA, many rows each) uses 4.  (One image's arithmetic depends on C only through these group
+  // sizes, the class split and the target's partial sums.)  Unrolling the Eq. 12/13 sums pays for
+  // the double-float form (FP32 pipes) and costs the FP64 form more than it gains (measured on
+  // GB300: 3.7 us per 7680x4320 image).
   constexpr int kSumUnroll = std::is_same<F, double>::value ? 1 : 4;
   auto group = [&](int own, int terms) {
     if (C == 1) return 4;
