@@ -62,3 +62,19 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(hr, "_LIB", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         hr.library()
+
+
+def test_noalloc_entry_point_validates_before_device_use(lib):
+    import paper_2510_21100_gb300 as hr
+    f = lib.histretinex_enhance_noalloc
+    f.argtypes = [ctypes.POINTER(hr.hr_params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                  ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]
+    ok = hr.Params().c()
+    big = hr.Params(K=512).c()
+    fake = ctypes.c_void_p(16)  # never dereferenced: every case below is refused first
+    assert f(ctypes.byref(big), fake, fake, 8, 8, 24, 24, 2, None) == hr.ERR_UNSUPPORTED  # K > 256
+    assert f(ctypes.byref(ok), None, fake, 8, 8, 24, 24, 1, None) == hr.ERR_INVALID_ARG
+    assert f(ctypes.byref(ok), fake, fake, 0, 8, 24, 24, 1, None) == hr.ERR_INVALID_ARG
+    assert f(ctypes.byref(ok), fake, fake, 8, 8, 20, 24, 1, None) == hr.ERR_INVALID_ARG  # pitch < 3 W
+    assert f(ctypes.byref(ok), fake, fake, 8, 8, 24, 24, 3, None) == hr.ERR_INVALID_ARG  # element size
+    assert f(ctypes.byref(ok), fake, fake, 65536, 32768, 196608, 196608, 1, None) == hr.ERR_UNSUPPORTED
