@@ -28,8 +28,10 @@
  *
  * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  * Device-side calls are asynchronous on that stream; argument errors are returned
- * synchronously; errors found by the kernels (a level >= K, a timed-out wait) are
- * recorded in a device status word and returned by histretinex_sync_status().
+ * synchronously; errors found by the kernels (a level >= K) are recorded in a device
+ * status word and returned by histretinex_sync_status().  The kernels wait only at
+ * hardware barriers (CTA and cluster barriers, copy completion), never in a spin loop;
+ * HR_ERR_TIMEOUT is kept for a bounded device-side wait and is not raised today.
  *
  * Ownership: the caller owns every image buffer; the context owns its device
  * workspace and per-K tables and frees them in histretinex_destroy().  A context is
@@ -52,7 +54,7 @@ typedef enum {
   HR_ERR_OOM = 3,          /* device or host allocation failed */
   HR_ERR_CUDA = 4,         /* a CUDA runtime call failed */
   HR_ERR_RANGE = 5,        /* an image held a level >= K */
-  HR_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up */
+  HR_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up (reserved: no kernel spins) */
 } hr_status;
 
 typedef enum {
