@@ -338,6 +338,10 @@ class Context:
         return {k: getattr(t, k) for k, _ in hr_tuning._fields_}
 
     def set_tuning(self, **kw):
+        """Changes launch shapes (histretinex_set_tuning; fields as in hr_tuning): hist_ctas_per_sm,
+        apply_ctas_per_sm (1..32), solve_cluster (1, 2, 4, 8, 16), use_graph (0/1), pdl (mask 0..7 of
+        the kernels launched as programmatic dependent launches), groups (1/2 for large batches).
+        Fields not given keep their current values; invalid values raise and change nothing."""
         cur = self.tuning()
         cur.update(kw)
         t = hr_tuning(**cur)
