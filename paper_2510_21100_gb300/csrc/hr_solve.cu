@@ -788,7 +788,9 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   // segment; many (a CTA alone) add into per-warp partial targets instead (a warp's rows in order,
   // then the warps in order), which spares the pass over all rows per class.
   const size_t room = (size_t)kPieceCap * (sizeof(F) + sizeof(uint2)) + (size_t)kListCap * sizeof(unsigned);
-  const bool few_rows = aB - aA <= 32;
+  // (decided from the largest own-row count, so every CTA of a cluster takes the same form: the
+  // workspace forms, row segments and per-CTA partial blocks, share one area of the slot)
+  const bool few_rows = (nR + C - 1) / C <= 32;
   F* seg_s = nullptr;
   F* wacc = nullptr;
   if (ob.s_part) {  // (s_part, s_piece and s_list are contiguous)
