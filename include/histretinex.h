@@ -170,13 +170,15 @@ hr_status histretinex_enhance_host_many(hr_ctx* ctx, int n, const void* const* h
  * histretinex_enhance) for K <= 256, with its whole workspace in one 1 MiB array that the library
  * declares in device memory; that array stays resident on every device that loads the library
  * until the process exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
- * K > 256 returns HR_ERR_UNSUPPORTED.  The first call on a device looks up the array's device
- * address (and the first call for a new (K, gamma) uploads the Eq. 19 table): make that first
- * call before any stream capture.  Every call uses the same array, which keeps the previous
- * call's contents (the call clears the histograms it accumulates); calls whose work overlaps on
- * the GPU (other streams, other threads) race on it and must be serialised by the caller.
- * Levels >= K are clamped but not reported.  Asynchronous on `stream`; the descriptor upload
- * from host memory waits for the stream's earlier work. */
+ * K > 256 returns HR_ERR_UNSUPPORTED.  Each call looks up the array's address on the current
+ * device (cudaGetSymbolAddress, which allocates nothing; the first call on a device may load the
+ * library's device code, so make it before any stream capture), then queues on `stream` two
+ * memsets (the histograms it accumulates and its status word) and four kernels (its own table of
+ * the class boundaries for its K and gamma, built from values passed by value, then the three
+ * pipeline stages): nothing it reads is left over from an earlier call.  Every call uses the same
+ * array, so calls whose work overlaps on the GPU (other streams, other threads) race on it and
+ * must be serialised by the caller.  Levels >= K are clamped but not reported.  Asynchronous on
+ * `stream`. */
 hr_status histretinex_enhance_noalloc(const hr_params* p, const void* d_in, void* d_out, int width, int height,
                                       size_t in_pitch, size_t out_pitch, int elem_bytes, void* stream);
 
@@ -225,6 +227,17 @@ hr_status histretinex_stage_times(hr_ctx* ctx, double* ms, int* calls, int reset
  * at its phase boundaries (set-up, each iteration's three barriers, target, LUT), written to ns;
  * *count is set to the number written.  Synchronises the device.  A measurement hook. */
 hr_status histretinex_profile_solve(hr_ctx* ctx, int image, long long* ns, int* count);
+
+/* Self-test hook, not part of the paper's method: the gradient level of step 1 -- the nearest
+ * integer to sqrt(m2), halves rounded up, clipped to K - 1 -- of every squared Sobel magnitude m2
+ * in [m2_first, m2_first + n), computed by the device code of one of the histogram kernels:
+ * form 0 that of the strip kernel (8-bit images: K <= 256; any m2 >= 0), form 1 that of the
+ * staged-tile kernel (8-bit images: K <= 256; m2 < 2^23), form 2 that of the generic kernel
+ * (K <= 4096; m2 < 2^31).  d_out: device array of n uint16 entries, d_out[t] = level of
+ * m2_first + t.  Asynchronous on `stream`.  HR_ERR_INVALID_ARG for an unknown form, K not a power
+ * of two in [8, 4096] (or above 256 for forms 0 and 1), m2_first < 0, n < 1, a null d_out or a
+ * range beyond the form's; HR_ERR_CUDA if the launch fails. */
+hr_status histretinex_gradient_levels(int form, int K, int m2_first, int n, uint16_t* d_out, void* stream);
 
 /* Number of kernels this library launched on the context since creation (for
  * launch accounting by callers and benchmarks). */

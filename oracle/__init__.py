@@ -37,7 +37,14 @@ class _Params(ctypes.Structure):
         ("eps", ctypes.c_double),
         ("max_iter", ctypes.c_int),
         ("fixed_iters", ctypes.c_int),
+        ("variants", ctypes.c_int),
     ]
+
+
+# Printed forms of three points the default readings settle otherwise (bits of Params.variants).
+VAR_PRINTED_UPDATE = 1     # Eq. 12 / Eq. 13 as printed: the weight K_ij divides
+VAR_NEAREST_MATCH = 2      # matching to the nearest cumulative share instead of the first that reaches it
+VAR_FORWARD_GRADIENT = 4   # the gradient image as forward differences instead of the Sobel operator
 
 
 @dataclass
@@ -51,9 +58,11 @@ class Params:
     eps: float = 0.0
     max_iter: int = 10
     fixed_iters: bool = True
+    variants: int = 0
 
     def c(self) -> _Params:
-        return _Params(self.K, self.alpha, self.beta, self.gamma, self.eps, self.max_iter, int(self.fixed_iters))
+        return _Params(self.K, self.alpha, self.beta, self.gamma, self.eps, self.max_iter, int(self.fixed_iters),
+                       int(self.variants))
 
 
 def build(force: bool = False) -> str:
@@ -81,6 +90,9 @@ def lib():
         L.orc_class_index.argtypes = [i, i, i]
         L.orc_class_index.restype = ctypes.c_uint32
         L.orc_iterate.argtypes = [vp, vp, i, d, d, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.orc_iterate_v.argtypes = [vp, vp, i, d, d, i, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.orc_histograms_v.argtypes = [vp, i, i, sz, i, i, i, vp, vp]
+        L.orc_lut_v.argtypes = [vp, vp, i, i, vp]
         L.orc_solve.argtypes = [vp, vp, ctypes.POINTER(_Params), vp, vp, ctypes.POINTER(ctypes.c_int)]
         L.orc_index1_table.argtypes = [i, d, vp]
         L.orc_target.argtypes = [vp, vp, i, d, ctypes.c_uint64, vp]
@@ -123,12 +135,13 @@ def value_channel(img: np.ndarray, K: int) -> np.ndarray:
     return V
 
 
-def histograms(img: np.ndarray, K: int):
-    """(S, G): Eq. 3 histogram of V and histogram of the gradient image, uint64[K] each."""
+def histograms(img: np.ndarray, K: int, forward: bool = False):
+    """(S, G): Eq. 3 histogram of V and histogram of the gradient image, uint64[K] each
+    (forward: forward-difference gradient instead of Sobel)."""
     img, W, H, pitch, eb = _img_args(img)
     S = np.zeros(K, dtype=np.uint64)
     G = np.zeros(K, dtype=np.uint64)
-    _check(lib().orc_histograms(_ptr(img), W, H, pitch, eb, K, _ptr(S), _ptr(G)))
+    _check(lib().orc_histograms_v(_ptr(img), W, H, pitch, eb, K, int(forward), _ptr(S), _ptr(G)))
     return S, G
 
 
@@ -136,15 +149,16 @@ def class_index(K: int, i: int, j: int) -> int:
     return int(lib().orc_class_index(K, i, j))
 
 
-def iterate(S, G, R, L, K: int, alpha: float, beta: float):
-    """One iteration of Algorithm 1; returns dict with P, q, Ru, Lu (before Eq. 14/15), Rn, Ln."""
+def iterate(S, G, R, L, K: int, alpha: float, beta: float, printed: bool = False):
+    """One iteration of Algorithm 1; returns dict with P, q, Ru, Lu (before Eq. 14/15), Rn, Ln
+    (printed: Eq. 12 / Eq. 13 as printed, the weight dividing)."""
     S = np.ascontiguousarray(S, dtype=np.uint64)
     G = np.ascontiguousarray(G, dtype=np.uint64)
     R = np.ascontiguousarray(R, dtype=np.float64)
     L = np.ascontiguousarray(L, dtype=np.float64)
     out = {k: np.zeros(K, dtype=np.float64) for k in ("P", "q", "Ru", "Lu", "Rn", "Ln")}
-    _check(lib().orc_iterate(_ptr(S), _ptr(G), K, alpha, beta, _ptr(R), _ptr(L), _ptr(out["P"]), _ptr(out["q"]),
-                             _ptr(out["Ru"]), _ptr(out["Lu"]), _ptr(out["Rn"]), _ptr(out["Ln"])))
+    _check(lib().orc_iterate_v(_ptr(S), _ptr(G), K, alpha, beta, int(printed), _ptr(R), _ptr(L), _ptr(out["P"]),
+                               _ptr(out["q"]), _ptr(out["Ru"]), _ptr(out["Lu"]), _ptr(out["Rn"]), _ptr(out["Ln"])))
     return out
 
 
@@ -175,12 +189,13 @@ def target(R, L, K: int, gamma: float, N: int) -> np.ndarray:
     return T
 
 
-def lut(S, T, K: int) -> np.ndarray:
-    """Histogram matching LUT from the histogram S of V to the target T."""
+def lut(S, T, K: int, nearest: bool = False) -> np.ndarray:
+    """Histogram matching LUT from the histogram S of V to the target T (nearest: the target level
+    of nearest cumulative share instead of the first that reaches the source's)."""
     S = np.ascontiguousarray(S, dtype=np.uint64)
     T = np.ascontiguousarray(T, dtype=np.float64)
     out = np.zeros(K, dtype=np.uint16)
-    _check(lib().orc_lut(_ptr(S), _ptr(T), K, _ptr(out)))
+    _check(lib().orc_lut_v(_ptr(S), _ptr(T), K, int(nearest), _ptr(out)))
     return out
 
 

@@ -21,7 +21,7 @@
  *   5. Histogram matching of V to that histogram, as a K-entry LUT      Sec. III.C (last paragraph)
  *   6. New V applied with hue and saturation kept                       Sec. II preamble, Sec. IV.A
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - location histogram H_B(X)_k = k/(K-1); the "/N" printed in Eq. 7 and Eq. 8 is dropped
  *     (with it every product would round to level 0; Eq. 18 has no /N);
  *   - index(i,j): i is the reflectance bin, j the illumination bin (Eq. 10);
@@ -59,7 +59,18 @@ typedef struct {
   double eps;       /* stopping threshold of Algorithm 1 */
   int max_iter;     /* T of Algorithm 1 */
   int fixed_iters;  /* nonzero: always run max_iter iterations */
+  int variants;     /* ORC_VAR_* bits: the printed forms instead of the default readings */
 } orc_params;
+
+/* Printed forms of three points the default readings settle otherwise (each selectable alone):
+ *   ORC_VAR_PRINTED_UPDATE   Eq. 12 and Eq. 13 exactly as printed, the weight K_ij dividing;
+ *   ORC_VAR_NEAREST_MATCH    histogram matching to the target level whose cumulative share is
+ *                            nearest to the source level's (Sec. III.C names matching only);
+ *   ORC_VAR_FORWARD_GRADIENT the gradient image as forward differences of V (Sec. III.B speaks
+ *                            of "the gradient image" without naming an operator). */
+#define ORC_VAR_PRINTED_UPDATE 1
+#define ORC_VAR_NEAREST_MATCH 2
+#define ORC_VAR_FORWARD_GRADIENT 4
 
 /* ---------- Stage 1-2: value channel, Eq. 3 histogram, gradient histogram ---------- */
 
@@ -89,14 +100,21 @@ static uint64_t isqrt_u64(uint64_t m) {
   return lo;
 }
 
-/* Gradient level of pixel (x,y): 3x3 Sobel on V with replicate border,
- * magnitude sqrt(gx^2 + gy^2) rounded half up, clipped to K-1. */
-static unsigned gradient_level(const unsigned* V, int W, int H, int x, int y, int K) {
+/* Gradient level of pixel (x,y): 3x3 Sobel on V with replicate border (forward = 0), or the
+ * forward differences gx = V(x+1,y) - V(x,y), gy = V(x,y+1) - V(x,y) with replicate border
+ * (forward = 1); magnitude sqrt(gx^2 + gy^2) rounded half up, clipped to K-1. */
+static unsigned gradient_level(const unsigned* V, int W, int H, int x, int y, int K, int forward) {
 #define VV(xx, yy) ((int64_t)V[(size_t)clampi((yy), 0, H - 1) * W + clampi((xx), 0, W - 1)])
-  int64_t gx = (VV(x + 1, y - 1) + 2 * VV(x + 1, y) + VV(x + 1, y + 1)) -
-               (VV(x - 1, y - 1) + 2 * VV(x - 1, y) + VV(x - 1, y + 1));
-  int64_t gy = (VV(x - 1, y + 1) + 2 * VV(x, y + 1) + VV(x + 1, y + 1)) -
-               (VV(x - 1, y - 1) + 2 * VV(x, y - 1) + VV(x + 1, y - 1));
+  int64_t gx, gy;
+  if (forward) {
+    gx = VV(x + 1, y) - VV(x, y);
+    gy = VV(x, y + 1) - VV(x, y);
+  } else {
+    gx = (VV(x + 1, y - 1) + 2 * VV(x + 1, y) + VV(x + 1, y + 1)) -
+         (VV(x - 1, y - 1) + 2 * VV(x - 1, y) + VV(x - 1, y + 1));
+    gy = (VV(x - 1, y + 1) + 2 * VV(x, y + 1) + VV(x + 1, y + 1)) -
+         (VV(x - 1, y - 1) + 2 * VV(x, y - 1) + VV(x + 1, y - 1));
+  }
 #undef VV
   uint64_t m2 = (uint64_t)(gx * gx) + (uint64_t)(gy * gy);
   uint64_t n = isqrt_u64(m2);
@@ -119,8 +137,10 @@ int orc_value_channel(const void* in, int W, int H, size_t pitch, int elem_bytes
   return bad ? ORC_ERR_RANGE : ORC_OK;
 }
 
-/* H_C(S) (Eq. 3) and H_C(grad S) (gradient histogram, Alg. 1 initialisation). */
-int orc_histograms(const void* in, int W, int H, size_t pitch, int elem_bytes, int K, uint64_t* S, uint64_t* G) {
+/* H_C(S) (Eq. 3) and H_C(grad S) (gradient histogram, Alg. 1 initialisation); forward selects
+ * the forward-difference gradient (ORC_VAR_FORWARD_GRADIENT) instead of the Sobel operator. */
+int orc_histograms_v(const void* in, int W, int H, size_t pitch, int elem_bytes, int K, int forward, uint64_t* S,
+                     uint64_t* G) {
   if (K < 2 || !S || !G) return ORC_ERR_INVALID_ARG;
   unsigned* V = (unsigned*)malloc(sizeof(unsigned) * (size_t)W * (size_t)H);
   if (!V) return ORC_ERR_INVALID_ARG;
@@ -131,10 +151,14 @@ int orc_histograms(const void* in, int W, int H, size_t pitch, int elem_bytes, i
   for (int y = 0; y < H; ++y)
     for (int x = 0; x < W; ++x) {
       S[V[(size_t)y * W + x]] += 1;
-      G[gradient_level(V, W, H, x, y, K)] += 1;
+      G[gradient_level(V, W, H, x, y, K, forward)] += 1;
     }
   free(V);
   return ORC_OK;
+}
+
+int orc_histograms(const void* in, int W, int H, size_t pitch, int elem_bytes, int K, uint64_t* S, uint64_t* G) {
+  return orc_histograms_v(in, W, H, pitch, elem_bytes, K, 0, S, G);
 }
 
 /* ---------- Stage 3: class map and the two-level optimisation ---------- */
@@ -153,10 +177,11 @@ uint32_t orc_class_index(int K, int i, int j) {
  * Out: P (Eq. 11 class totals of the count matrix, times N), q (S_k / P_k),
  *      Ru, Lu (Eq. 13 and Eq. 12 results before renormalisation),
  *      Rn, Ln (Eq. 15 and Eq. 14 results).
- * Any output pointer except Rn, Ln may be NULL. */
-int orc_iterate(const uint64_t* S, const uint64_t* G, int K, double alpha, double beta,
-                const double* R, const double* L, double* P_out, double* q_out,
-                double* Ru_out, double* Lu_out, double* Rn, double* Ln) {
+ * Any output pointer except Rn, Ln may be NULL.  printed != 0 takes Eq. 13 and Eq. 12 as printed
+ * (ORC_VAR_PRINTED_UPDATE): the weight K_ij divides the data term instead of multiplying it. */
+int orc_iterate_v(const uint64_t* S, const uint64_t* G, int K, double alpha, double beta, int printed,
+                  const double* R, const double* L, double* P_out, double* q_out,
+                  double* Ru_out, double* Lu_out, double* Rn, double* Ln) {
   if (K < 2 || !S || !G || !R || !L || !Rn || !Ln) return ORC_ERR_INVALID_ARG;
   uint64_t Nu = 0;
   for (int k = 0; k < K; ++k) Nu += S[k];
@@ -186,7 +211,38 @@ int orc_iterate(const uint64_t* S, const uint64_t* G, int K, double alpha, doubl
   for (int j = 0; j < K; ++j) sL2 = fma(L[j], L[j], sL2);
   const double dR = sL2 / NN + beta;
   for (int j = 0; j < K; ++j) L2[j] = L[j] * L[j];
-  for (int i = 0; i < K; ++i) {
+  if (printed) {
+    /* Eq. 13 and Eq. 12 as printed:
+     *   H_C(R)_i = (sum_j H_C(L)_j H_C(S)_idx(i,j) / (N K_ij) + beta H_C(grad S)_i) / (sum_j H_C(L)_j^2 / N^2 + beta)
+     *   H_C(L)_j = (sum_i H_C(R)_i H_C(S)_idx(i,j) / (N K_ij) + alpha H_C(S)_j) / (sum_i H_C(R)_i^2 / N^2 + alpha)
+     * with K_ij = H_C(L,R)_ij / (class total of H_C(L,R)) by Eq. 11 (H_C(L,R)_ij = R_i L_j / N, Eq. 6)
+     * from the previous iterate, the new R in the L update (Algorithm 1 order); a cell whose
+     * weight is zero contributes nothing (the printed quotient is undefined there). */
+    for (int i = 0; i < K; ++i) {
+      double A = 0.0;
+      for (int j = 0; j < K; ++j) {
+        const uint32_t k = orc_class_index(K, i, j);
+        const double Kij = P[k] > 0.0 ? ((R[i] * L[j]) / N) / (P[k] / N) : 0.0;
+        if (Kij == 0.0) continue;
+        A += (L[j] * (double)S[k]) / (N * Kij);
+      }
+      Ru[i] = (A + beta * (double)G[i]) / dR;
+    }
+    double sR2p = 0.0;
+    for (int i = 0; i < K; ++i) sR2p = fma(Ru[i], Ru[i], sR2p);
+    const double dLp = sR2p / NN + alpha;
+    for (int j = 0; j < K; ++j) {
+      double B = 0.0;
+      for (int i = 0; i < K; ++i) {
+        const uint32_t k = orc_class_index(K, i, j);
+        const double Kij = P[k] > 0.0 ? ((R[i] * L[j]) / N) / (P[k] / N) : 0.0;
+        if (Kij == 0.0) continue;
+        B += (Ru[i] * (double)S[k]) / (N * Kij);
+      }
+      Lu[j] = (B + alpha * (double)S[j]) / dLp;
+    }
+  }
+  for (int i = 0; i < K && !printed; ++i) {
     double A = 0.0;
     for (int j = 0; j < K; ++j) {
       double qk = q[orc_class_index(K, i, j)];
@@ -201,7 +257,7 @@ int orc_iterate(const uint64_t* S, const uint64_t* G, int K, double alpha, doubl
   for (int i = 0; i < K; ++i) sR2 = fma(Ru[i], Ru[i], sR2);
   const double dL = sR2 / NN + alpha;
   for (int i = 0; i < K; ++i) RR[i] = Ru[i] * R[i];
-  for (int j = 0; j < K; ++j) {
+  for (int j = 0; j < K && !printed; ++j) {
     double B = 0.0;
     for (int i = 0; i < K; ++i) {
       double qk = q[orc_class_index(K, i, j)];
@@ -226,6 +282,12 @@ int orc_iterate(const uint64_t* S, const uint64_t* G, int K, double alpha, doubl
   return ORC_OK;
 }
 
+int orc_iterate(const uint64_t* S, const uint64_t* G, int K, double alpha, double beta,
+                const double* R, const double* L, double* P_out, double* q_out,
+                double* Ru_out, double* Lu_out, double* Rn, double* Ln) {
+  return orc_iterate_v(S, G, K, alpha, beta, 0, R, L, P_out, q_out, Ru_out, Lu_out, Rn, Ln);
+}
+
 /* Algorithm 1: R^(0) = H_C(grad S), L^(0) = H_C(S); repeat the iteration until both
  * squared changes are <= eps, or max_iter iterations have run. */
 int orc_solve(const uint64_t* S, const uint64_t* G, const orc_params* p, double* R, double* L, int* iters) {
@@ -240,7 +302,8 @@ int orc_solve(const uint64_t* S, const uint64_t* G, const orc_params* p, double*
   for (int k = 0; k < K; ++k) { R[k] = (double)G[k]; L[k] = (double)S[k]; }
   int t = 0;
   while (t < p->max_iter) {
-    orc_iterate(S, G, K, p->alpha, p->beta, R, L, NULL, NULL, NULL, NULL, Rn, Ln);
+    orc_iterate_v(S, G, K, p->alpha, p->beta, (p->variants & ORC_VAR_PRINTED_UPDATE) != 0, R, L, NULL, NULL, NULL,
+                  NULL, Rn, Ln);
     double dr = 0.0, dl = 0.0;
     for (int i = 0; i < K; ++i) { double d = Rn[i] - R[i]; dr = fma(d, d, dr); }
     for (int j = 0; j < K; ++j) { double d = Ln[j] - L[j]; dl = fma(d, d, dl); }
@@ -320,8 +383,11 @@ int orc_target(const double* R, const double* L, int K, double gamma, uint64_t N
  * count of S, CT the cumulative sum of the target (ascending), TT = CT(K-1); K-1 if none.
  * Where CS(s) = N the condition is CT(z) >= TT, which in exact arithmetic holds from the last
  * occupied target level z_top on; that level is used directly, because a running FP64 sum
- * can absorb trailing bins far below its ulp and reach TT earlier. */
-int orc_lut(const uint64_t* S, const double* T, int K, uint16_t* lut) {
+ * can absorb trailing bins far below its ulp and reach TT earlier.
+ * nearest != 0 (ORC_VAR_NEAREST_MATCH): LUT[s] = the first z minimising |CT(z) * N - CS(s) * TT|,
+ * the target level whose cumulative share is nearest to the source level's (z_top where
+ * CS(s) = N, as above). */
+int orc_lut_v(const uint64_t* S, const double* T, int K, int nearest, uint16_t* lut) {
   if (K < 2 || K > 65536 || !S || !T || !lut) return ORC_ERR_INVALID_ARG;
   double* CT = (double*)malloc(sizeof(double) * (size_t)K);
   if (!CT) return ORC_ERR_INVALID_ARG;
@@ -339,12 +405,22 @@ int orc_lut(const uint64_t* S, const double* T, int K, uint16_t* lut) {
     if (cs == N) { lut[s] = (uint16_t)z_top; continue; }
     const double rhs = (double)cs * TT;
     int z = 0;
-    while (z < K - 1 && !(CT[z] * Nd >= rhs)) ++z;
+    if (nearest) {
+      double best = fabs(CT[0] * Nd - rhs);
+      for (int zz = 1; zz < K; ++zz) {
+        const double d = fabs(CT[zz] * Nd - rhs);
+        if (d < best) { best = d; z = zz; }
+      }
+    } else {
+      while (z < K - 1 && !(CT[z] * Nd >= rhs)) ++z;
+    }
     lut[s] = (uint16_t)z;
   }
   free(CT);
   return ORC_OK;
 }
+
+int orc_lut(const uint64_t* S, const double* T, int K, uint16_t* lut) { return orc_lut_v(S, T, K, 0, lut); }
 
 /* ---------- Stage 6: apply with hue and saturation kept ---------- */
 
@@ -383,13 +459,13 @@ int orc_enhance(const void* in, void* out, int W, int H, size_t in_pitch, size_t
                 uint16_t* lut, int* iters) {
   if (!p) return ORC_ERR_INVALID_ARG;
   const int K = p->K;
-  int st = orc_histograms(in, W, H, in_pitch, elem_bytes, K, S, G);
+  int st = orc_histograms_v(in, W, H, in_pitch, elem_bytes, K, (p->variants & ORC_VAR_FORWARD_GRADIENT) != 0, S, G);
   if (st != ORC_OK) return st;
   st = orc_solve(S, G, p, R, L, iters);
   if (st != ORC_OK) return st;
   st = orc_target(R, L, K, p->gamma, (uint64_t)W * (uint64_t)H, T);
   if (st != ORC_OK) return st;
-  st = orc_lut(S, T, K, lut);
+  st = orc_lut_v(S, T, K, (p->variants & ORC_VAR_NEAREST_MATCH) != 0, lut);
   if (st != ORC_OK) return st;
   return orc_apply(in, out, W, H, in_pitch, out_pitch, elem_bytes, K, lut);
 }

@@ -25,7 +25,7 @@ EXPORTS = (
     "histretinex_status_string", "histretinex_kernel_launches", "histretinex_stage_times",
     "histretinex_profile_solve", "histretinex_set_tuning", "histretinex_get_tuning",
     "histretinex_workspace_bytes", "histretinex_enhance_noalloc", "histretinex_reserve",
-    "histretinex_enhance_host_many",
+    "histretinex_enhance_host_many", "histretinex_gradient_levels",
 )
 
 
@@ -101,6 +101,8 @@ def _lib():
         L.histretinex_enhance_noalloc.restype = ctypes.c_int
         L.histretinex_reserve.argtypes = [vp, i]
         L.histretinex_reserve.restype = ctypes.c_int
+        L.histretinex_gradient_levels.argtypes = [i, i, i, i, vp, vp]
+        L.histretinex_gradient_levels.restype = ctypes.c_int
         L.histretinex_workspace_bytes.argtypes = [vp]
         L.histretinex_workspace_bytes.restype = ctypes.c_size_t
         for name in ("histretinex_create", "histretinex_enhance", "histretinex_enhance_batch",
@@ -193,6 +195,17 @@ def enhance_noalloc(d_in, d_out, params: "Params | None" = None, stream=None):
                                               ctypes.c_void_p(d_out.data_ptr()), W, H, pin, pout, eb,
                                               _stream_ptr(stream)), "histretinex_enhance_noalloc")
     return d_out
+
+
+def gradient_levels(form: int, K: int, m2_first: int, n: int, stream=None):
+    """histretinex_gradient_levels: the gradient levels of m2 in [m2_first, m2_first + n) by the
+    device code of histogram kernel form 0 (strips), 1 (staged tiles) or 2 (generic), as a
+    uint16 tensor on the current device (a self-test hook)."""
+    import torch
+    out = torch.empty(n, dtype=torch.uint16, device="cuda")
+    _check(_lib().histretinex_gradient_levels(form, K, m2_first, n, ctypes.c_void_p(out.data_ptr()),
+                                              _stream_ptr(stream)), "histretinex_gradient_levels")
+    return out
 
 
 class Context:

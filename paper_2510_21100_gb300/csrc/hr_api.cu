@@ -60,7 +60,7 @@ struct hr_ctx {
 
 namespace hr {
 
-static bool pow2(int k) { return k > 0 && (k & (k - 1)) == 0; }
+bool pow2(int k) { return k > 0 && (k & (k - 1)) == 0; }
 
 hr_status check_params(const hr_params* p) {
   if (!p) return HR_ERR_INVALID_ARG;
@@ -147,6 +147,9 @@ SlotLayout make_layout(int K) {
 namespace {
 
 hr_status cuda_fail(cudaError_t e) {
+  // a failed runtime call also leaves its error as the thread's last error; a non-sticky one (an
+  // allocation failure) is cleared so that it is not reported again by a later, unrelated check
+  if (e != cudaSuccess) cudaGetLastError();
   if (e == cudaErrorMemoryAllocation) return HR_ERR_OOM;
   return e == cudaSuccess ? HR_OK : HR_ERR_CUDA;
 }
@@ -779,5 +782,15 @@ hr_status histretinex_stage_times(hr_ctx* c, double* ms, int* calls, int reset) 
 }
 
 uint64_t histretinex_kernel_launches(const hr_ctx* c) { return c ? c->launches : 0; }
+
+hr_status histretinex_gradient_levels(int form, int K, int m2_first, int n, uint16_t* d_out, void* stream) {
+  if (form < 0 || form > 2 || !hr::pow2(K) || K < 8 || K > 4096 || m2_first < 0 || n < 1 || !d_out)
+    return HR_ERR_INVALID_ARG;
+  if (form < 2 && K > 256) return HR_ERR_INVALID_ARG;
+  const long long last = (long long)m2_first + n - 1;
+  if (last >= (form == 1 ? (1LL << 23) : (1LL << 31) - 1)) return HR_ERR_INVALID_ARG;
+  HR_CUDA(hr::launch_grad_level_probe(form, K, m2_first, n, d_out, static_cast<cudaStream_t>(stream)));
+  return HR_OK;
+}
 
 }  // extern "C"

@@ -135,6 +135,9 @@ cudaError_t launch_solve(const SolveArgs& a, int n, int cluster, cudaStream_t st
 cudaError_t launch_apply(const ImgTab& tab, int total_tiles, int elem_bytes, int K, uint8_t* slots, size_t slot_bytes,
                          SlotLayout lay, unsigned* status, int sms, int ctas_per_sm, cudaStream_t st, bool fast,
                          bool pdl);
+// Gradient levels of squared magnitudes [m2_first, m2_first + n) by one of the histogram kernels'
+// three device forms (0: strip kernel, 1: staged-tile kernel, 2: generic kernel), into out[n].
+cudaError_t launch_grad_level_probe(int form, int K, int m2_first, int n, uint16_t* out, cudaStream_t st);
 size_t solve_smem_bytes(int K, int vec_in_smem, int list_in_smem, size_t fsize);
 
 // Geometry of the pixel passes: tiles of kTileW x kTileH pixels.

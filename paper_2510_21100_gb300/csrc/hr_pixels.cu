@@ -5,6 +5,8 @@
 //            are kept (Sec. II preamble; Sec. III.C last paragraph: histogram matching).
 // Both kernels walk a flat list of kTileW x kTileH tiles spanning every image of the launch, so
 // one launch serves a single image or a batch of mixed sizes.
+#include <algorithm>
+
 #include "hr_internal.cuh"
 
 namespace hr {
@@ -377,12 +379,15 @@ __device__ __forceinline__ void red_shared(unsigned addr) {
 // relative of sqrt(m2) there, well inside the distance 1/(4 sqrt(m2) + 2) from sqrt(m2) to the
 // nearest half integer, so the round-to-nearest add of 2^23 yields the exact level
 // (0x4B000000 + level in the float's bits; hg_adj absorbs the 0x4B000000).
-__device__ __forceinline__ void count_px(int m2, unsigned v, int mclip, unsigned hs_sh, unsigned hg_adj, bool on) {
+__device__ __forceinline__ unsigned strip_grad_bits(int m2, int mclip) {
   const int m2c = min(m2, mclip);
   const float f = __fsub_rn(__int_as_float(0x4B000000 | m2c), 8388608.0f);
   float s;
   asm("sqrt.approx.f32 %0, %1;" : "=f"(s) : "f"(f));
-  const unsigned gb = __float_as_uint(__fadd_rn(s, 8388608.0f));
+  return __float_as_uint(__fadd_rn(s, 8388608.0f));
+}
+__device__ __forceinline__ void count_px(int m2, unsigned v, int mclip, unsigned hs_sh, unsigned hg_adj, bool on) {
+  const unsigned gb = strip_grad_bits(m2, mclip);
   if (on) {
     red_shared(hg_adj + (gb << 2));
     red_shared(hs_sh + (v << 2));
@@ -846,7 +851,32 @@ __global__ void __launch_bounds__(kThreads) apply_u8v_kernel(const ImgTab tab, i
   if (range_bad) atomicOr(status, kStRange);
 }
 
+// Self-test of the three gradient-level forms above (a test hook, not part of the method): the level
+// of every squared Sobel magnitude m2 in [m2_first, m2_first + n), by form 0 (strip kernel), 1
+// (staged-tile kernel) or 2 (generic kernel), written to out[m2 - m2_first].
+__global__ void grad_level_probe_kernel(int form, int K, int m2_first, int n, uint16_t* out) {
+  const int mclip = K * K - K;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int m2 = m2_first + t;
+    unsigned g;
+    if (form == 0) {
+      g = strip_grad_bits(m2, mclip) - 0x4B000000u;
+    } else if (form == 1) {
+      g = grad_level(m2, K);
+    } else {
+      g = round_sqrt((unsigned)m2);
+      g = g < (unsigned)(K - 1) ? g : (unsigned)(K - 1);
+    }
+    out[t] = (uint16_t)g;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_grad_level_probe(int form, int K, int m2_first, int n, uint16_t* out, cudaStream_t st) {
+  const int blocks = (int)std::min<long long>(4096, ((long long)n + 255) / 256);
+  return launch_kernel(grad_level_probe_kernel, dim3(blocks), dim3(256), 0, st, false, form, K, m2_first, n, out);
+}
 
 cudaError_t launch_hist(const ImgTab& tab, int total_tiles, int total_units, int interior_units, int elem_bytes,
                         int K, uint8_t* slots,

@@ -151,3 +151,74 @@ def apply(img, lut_):
             else:
                 out[y, x] = [math.floor(Fraction(ch * Vp, V) + Fraction(1, 2)) for ch in c]
     return out
+
+
+# ---- printed forms of three readings (selectable variants) ----
+
+def forward_levels(V, K):
+    """Gradient levels from forward differences gx = V(x+1,y) - V(x,y), gy = V(x,y+1) - V(x,y)
+    (replicate border: zero at the last column / row), magnitude rounded half up, clipped."""
+    P = np.pad(V.astype(np.int64), ((0, 1), (0, 1)), mode="edge")
+    H, W = V.shape
+    gx = P[:H, 1:W + 1] - P[:H, :W]
+    gy = P[1:H + 1, :W] - P[:H, :W]
+    out = np.zeros_like(V, dtype=np.int64)
+    for y in range(H):
+        for x in range(W):
+            m2 = int(gx[y, x]) ** 2 + int(gy[y, x]) ** 2
+            n = math.isqrt(m2)
+            out[y, x] = min(n + 1 if 4 * m2 >= (2 * n + 1) ** 2 else n, K - 1)
+    return out
+
+
+def iterate_printed_exact(S, G, R, L, alpha, beta, idx):
+    """One pass of Algorithm 1 with Eq. 13 and Eq. 12 exactly as printed (the weight K_ij divides),
+    in exact rational arithmetic over the given double inputs: K_ij = HCM_ij / class total
+    (Eq. 11, HCM_ij = R_i L_j / N by Eq. 6); a cell with zero weight contributes nothing.
+    Returns (Ru, Lu) as lists of Fractions."""
+    K = len(S)
+    N = Fraction(int(np.sum(S)))
+    Rf = [Fraction(float(x)) for x in R]
+    Lf = [Fraction(float(x)) for x in L]
+    Sf = [Fraction(int(x)) for x in S]
+    Gf = [Fraction(int(x)) for x in G]
+    hcm = [[Rf[i] * Lf[j] / N for j in range(K)] for i in range(K)]
+    tot = [Fraction(0)] * K
+    for i in range(K):
+        for j in range(K):
+            tot[idx[i][j]] += hcm[i][j]
+    W = [[(hcm[i][j] / tot[idx[i][j]]) if tot[idx[i][j]] != 0 else Fraction(0) for j in range(K)] for i in range(K)]
+    dR = sum(x * x for x in Lf) / (N * N) + Fraction(beta)
+    Ru = []
+    for i in range(K):
+        a = sum((Lf[j] * Sf[idx[i][j]] / (N * W[i][j]) for j in range(K) if W[i][j] != 0), Fraction(0))
+        Ru.append((a + Fraction(beta) * Gf[i]) / dR)
+    dL = sum(x * x for x in Ru) / (N * N) + Fraction(alpha)
+    Lu = []
+    for j in range(K):
+        b = sum((Ru[i] * Sf[idx[i][j]] / (N * W[i][j]) for i in range(K) if W[i][j] != 0), Fraction(0))
+        Lu.append((b + Fraction(alpha) * Sf[j]) / dL)
+    return Ru, Lu
+
+
+def lut_nearest(S, T):
+    """Target level whose cumulative share is nearest to the source level's: the first z minimising
+    |CT(z) N - CS(s) TT| in exact rational arithmetic over the given (double) target values; the
+    last occupied target level where CS(s) = N."""
+    K = len(S)
+    N = int(np.sum(S))
+    CT, acc = [], Fraction(0)
+    for t in T:
+        acc += Fraction(float(t))
+        CT.append(acc)
+    TT = CT[-1]
+    top = max(z for z in range(K) if T[z] > 0)
+    CS = np.cumsum(np.asarray(S, dtype=np.int64))
+    out = np.zeros(K, dtype=np.int64)
+    for s in range(K):
+        if int(CS[s]) == N:
+            out[s] = top
+            continue
+        d = [abs(CT[z] * N - int(CS[s]) * TT) for z in range(K)]
+        out[s] = d.index(min(d))
+    return out

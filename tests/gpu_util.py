@@ -11,9 +11,6 @@ import oracle
 # iterations of a contraction keep the difference at that level: 2 * 65536 * 1.1e-16 = 1.5e-11,
 # so 1e-9 leaves a wide margin while still catching any wrong term (which moves values by >> 1e-6).
 RTOL = 1e-9
-# A LUT decision CT(z) N >= CS(s) TT whose two sides lie closer than this (relative) can
-# legitimately flip under the tolerance above; all others must match exactly.
-LUT_MARGIN = 1e-7
 
 
 def params_pair(**kw):
@@ -24,21 +21,16 @@ def params_pair(**kw):
     return p, po
 
 
-def ambiguous_lut_levels(S, T):
-    """Levels s whose LUT decision lies within LUT_MARGIN of a tie, from the oracle's S and T."""
+def lut_decision_margin(S, T, s):
+    """Smallest relative distance |CT(z) N - CS(s) TT| / (CS(s) TT) over the levels z, for the
+    matching decision of source level s (the oracle's S and T).  A GPU LUT entry that differs
+    from the oracle's where this margin is far above RTOL is a bug; where it is below, the two
+    FP64 orders of summation could legitimately decide differently (a genuine near-tie)."""
     N = float(np.sum(S))
     CT = np.cumsum(np.asarray(T, dtype=np.float64))
-    TT = CT[-1]
-    CS = np.cumsum(np.asarray(S, dtype=np.float64))
-    lhs = CT * N
-    amb = []
-    for s in range(len(S)):
-        if CS[s] == N:  # top of the source CDF: decided exactly (last occupied target level)
-            continue
-        rhs = CS[s] * TT
-        if np.any(np.abs(lhs - rhs) <= LUT_MARGIN * max(abs(rhs), 1.0)):
-            amb.append(s)
-    return set(amb)
+    CS = float(np.sum(np.asarray(S, dtype=np.float64)[: s + 1]))
+    rhs = CS * CT[-1]
+    return float(np.min(np.abs(CT * N - rhs)) / max(rhs, 1e-300))
 
 
 def assert_close(got, want, what):
@@ -51,10 +43,23 @@ def assert_close(got, want, what):
         assert err <= RTOL, f"{what}: max relative error {err:.3e} > {RTOL}"
 
 
+def assert_lut_equal(lut, ref_S, ref_T, ref_lut, what="LUT"):
+    """The plain form's LUT must equal the oracle's entry for entry.  A differing entry fails
+    the test; the message says whether the oracle's decision there was a genuine FP64 near-tie
+    (margin below 1e-9) or not."""
+    lut = np.asarray(lut, dtype=np.int64)
+    ref = np.asarray(ref_lut, dtype=np.int64)
+    diff = np.nonzero(lut != ref)[0]
+    if diff.size:
+        info = [(int(s), int(lut[s]), int(ref[s]), lut_decision_margin(ref_S, ref_T, int(s))) for s in diff[:8]]
+        kinds = ["near-tie" if m < RTOL else "not a tie" for *_, m in info]
+        raise AssertionError(f"{what} differs from the oracle at {diff.size} levels: "
+                             f"(level, gpu, oracle, decision margin) {info} -> {kinds}")
+
+
 def compare_to_oracle(img: np.ndarray, out: np.ndarray, dbg: dict, po, check_fp=True):
-    """Parity of one image: histograms exact, R/L/T within RTOL, LUT exact away from ties,
-    output pixels exact (against the oracle's apply of the GPU's own LUT, and against the
-    oracle's output wherever the LUTs agree)."""
+    """Parity of one image with the oracle: histograms, LUT and output pixels bit-exact; R, L and
+    the enhanced histogram within RTOL."""
     ref = oracle.enhance(img, po)
     assert np.array_equal(dbg["S"], ref.S), "H_C(S) differs"
     assert np.array_equal(dbg["G"], ref.G), "H_C(grad S) differs"
@@ -63,14 +68,8 @@ def compare_to_oracle(img: np.ndarray, out: np.ndarray, dbg: dict, po, check_fp=
         assert_close(dbg["R"], ref.R, "H_C(R)")
         assert_close(dbg["L"], ref.L, "H_C(L)")
         assert_close(dbg["T"], ref.T, "enhanced histogram")
-    amb = ambiguous_lut_levels(ref.S, ref.T)
-    lut = dbg["lut"].astype(np.int64)
-    diff = np.nonzero(lut != ref.lut.astype(np.int64))[0]
-    bad = [int(s) for s in diff if s not in amb or abs(int(lut[s]) - int(ref.lut[s])) > 1]
-    assert not bad, f"LUT differs at non-tie levels {bad[:10]}"
-    assert np.array_equal(out, oracle.apply(img, dbg["lut"], po.K)), "apply differs from the oracle's apply"
-    if diff.size == 0:
-        assert np.array_equal(out, ref.out), "output pixels differ"
+    assert_lut_equal(dbg["lut"], ref.S, ref.T, ref.lut)
+    assert np.array_equal(out, ref.out), "output pixels differ from the oracle's"
     return ref
 
 

@@ -36,9 +36,9 @@ def near_tie_levels(S, T):
     return out
 
 
-def check_precision(img, out, dbg, K, **kw):
-    po = oracle.Params(K=K, **kw)
-    ref = oracle.enhance(img, po)
+def check_precision(img, out, dbg, K, ref=None, **kw):
+    if ref is None:
+        ref = oracle.enhance(img, oracle.Params(K=K, **kw))
     assert np.array_equal(dbg["S"], ref.S) and np.array_equal(dbg["G"], ref.G)
     err = np.max(np.abs(dbg["T"] - ref.T) / np.maximum(ref.T, 1.0))
     assert err <= T_RTOL, f"target rel err {err:.2e}"
@@ -70,6 +70,33 @@ def test_fp32_form_12bit_k4096_batch(hr):
     ctx.check()
     for i, im in enumerate(imgs):
         check_precision(im, outs[i].cpu().numpy(), ctx.debug(i), 4096)
+
+
+def test_fp32_form_at_the_12bit_k4096_workload_size(hr):
+    """The reduced-precision form at its own workload's size: 1000x664 12-bit images, K = 4096,
+    T = 10.  Three images in one batch call on one CTA each (the path of the 1024-image batch:
+    cell lists, pieces and the Eq. 19 partials in the global workspace, whole supports of about
+    1700 x 2100 cells) and one image alone on its 16-CTA cluster; each against the FP64 oracle
+    (run on three host threads: the oracle's K^2 loops take seconds per image here)."""
+    import concurrent.futures as cf
+    import torch
+    imgs = [synth.low_light_image(1000, 664, seed=synth.seed_for(3, i), bits=12) for i in range(3)]
+    po = oracle.Params(K=4096)
+    with cf.ThreadPoolExecutor(3) as ex:
+        refs = list(ex.map(lambda im: oracle.enhance(im, po), imgs))
+    ctx = hr.Context(hr.Params(K=4096, precision=hr.PREC_FP32, debug=True))
+    ctx.set_tuning(solve_cluster=1)
+    outs = ctx.enhance_batch([hr.to_device_aligned(im) for im in imgs],
+                             [hr.aligned_empty(664, 1000, dtype=torch.uint16) for _ in imgs])
+    ctx.check()
+    report = []
+    for i, im in enumerate(imgs):
+        report.append(check_precision(im, outs[i].cpu().numpy(), ctx.debug(i), 4096, ref=refs[i]))
+    alone = hr.Context(hr.Params(K=4096, precision=hr.PREC_FP32, debug=True))
+    out0 = alone.enhance(hr.to_device_aligned(imgs[0]), hr.aligned_empty(664, 1000, dtype=torch.uint16))
+    alone.check()
+    report.append(check_precision(imgs[0], out0.cpu().numpy(), alone.debug(0), 4096, ref=refs[0]))
+    print("FP32 form at 1000x664, K = 4096: (max rel err of T, LUT entries differing) per image:", report)
 
 
 def test_fp32_and_fp64_forms_agree_on_pixels_mostly(hr):
