@@ -40,13 +40,16 @@ def parse():
     ap.add_argument("--width", type=int, default=7680)
     ap.add_argument("--height", type=int, default=4320)
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, per-size and CPU-baseline legs")
+    ap.add_argument("--streams", type=int, default=4, help="CUDA streams the timed steps go to, round-robin")
     return ap.parse_args()
 
 
-def workload_config(W, H):
+def workload_config(W, H, streams=1):
     return {"workload": f"plain single image {W}x{H} uint8 RGB, K=256, T=10 fixed iterations, gamma=2.2, "
-                        f"alpha=beta=1e-3; 3 rotating input/output buffers (inputs larger than L2 in aggregate)",
-            "image": f"{W}x{H}", "K": 256, "iterations": 10, "elem": "uint8", "l2": "rotating inputs > L2"}
+                        f"alpha=beta=1e-3, FP64 solve; one histretinex_enhance call per step, steps round-robin on "
+                        f"{streams} CUDA stream(s); 3 rotating input/output buffers (inputs larger than L2 in aggregate)",
+            "image": f"{W}x{H}", "K": 256, "iterations": 10, "elem": "uint8", "l2": "rotating inputs > L2",
+            "streams": streams}
 
 
 def make_images(W, H, rank=0):
@@ -156,7 +159,7 @@ def run_reference(a, rank, world):
     sample = f"rows 0-{rows - 1} of the {W}x{H} image ({rows * W / 1e6:.2f} MP) per step, single-threaded FP64 C oracle"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": el * 1000 / a.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(W, H),
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(W, H, a.streams),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -296,10 +299,21 @@ def serving_leg(torch, hr, local, big_img, seconds=5.0, rate=400.0, seed=5):
     return out
 
 
-def timed_loop(ctx, dins, douts, steps, warmup, dist, torch, staged=False):
+def timed_loop(ctx, dins, douts, steps, warmup, dist, torch, staged=False, n_streams=1):
+    """K steps (one image each) between CUDA events on the current stream.  With n_streams > 1 the
+    steps go round-robin to that many streams (buffer pair k on stream k, so no buffer crosses
+    streams), which start after the first event and end before the second: calls on different
+    streams overlap on the device (one image's solve beside other images' pixel passes)."""
     n = len(dins)
+    main_st = torch.cuda.current_stream()
+    sts = [main_st] + [torch.cuda.Stream() for _ in range(n_streams - 1)]
+
+    def issue(k):
+        st = sts[k % n_streams]
+        ctx.enhance(dins[k % n], douts[k % n], stream=st)
+
     for s in range(warmup):
-        ctx.enhance(dins[s % n], douts[s % n])
+        issue(s)
     torch.cuda.synchronize()
     if staged:
         ctx.stage_times(reset=True)
@@ -308,10 +322,16 @@ def timed_loop(ctx, dins, douts, steps, warmup, dist, torch, staged=False):
     torch.cuda.synchronize()
     l0 = ctx.kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
+    e0.record(main_st)
+    for st in sts[1:]:
+        st.wait_event(e0)
     for s in range(steps):
-        ctx.enhance(dins[s % n], douts[s % n])
-    e1.record()
+        issue(s)
+    for st in sts[1:]:
+        ev = torch.cuda.Event()
+        ev.record(st)
+        main_st.wait_event(ev)
+    e1.record(main_st)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -322,6 +342,23 @@ def timed_loop(ctx, dins, douts, steps, warmup, dist, torch, staged=False):
         return ms_total, launches, None
     h, so, ap, calls = ctx.stage_times(reset=True)
     return ms_total, launches, (h / calls, so / calls, ap / calls)
+
+
+def latency_ms(ctx, din, dout, reps, torch):
+    """Per-image latency: one call at a time, each timed alone between events (mean, p50, max)."""
+    for _ in range(3):
+        ctx.enhance(din, dout)
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.enhance(din, dout)
+        e1.record()
+        e1.synchronize()
+        t.append(e0.elapsed_time(e1))
+    t.sort()
+    return {"mean": sum(t) / len(t), "p50": t[len(t) // 2], "max": t[-1], "calls": reps}
 
 
 def main():
@@ -365,9 +402,12 @@ def main():
     except Exception:
         uuid = None
     sampler = ClockSampler(uuid).__enter__()
-    ms_total, launches, _ = timed_loop(ctx, dins, douts, a.steps, a.warmup, dist, torch)
-    ms_staged, _, stage = timed_loop(sctx, dins, douts, a.steps, a.warmup, dist, torch, staged=True)
+    ms_total, launches, _ = timed_loop(ctx, dins, douts, a.steps, a.warmup, dist, torch, n_streams=a.streams)
     clocks = sampler.result()
+    ms_one, _, _ = timed_loop(ctx, dins, douts, a.steps, a.warmup, dist, torch, n_streams=1)
+    ms_staged, _, stage = timed_loop(sctx, dins, douts, a.steps, a.warmup, dist, torch, staged=True)
+    lat = latency_ms(ctx, dins[0], douts[0], max(20, min(100, a.steps // 4)), torch)
+    part_info = ctx.partition_info()
 
     from paper_2510_21100_gb300 import shard
     ms_step = shard.max_over_ranks(ms_total / a.steps, dist, device="cuda")
@@ -409,8 +449,14 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-        "data": "synthetic", "config": workload_config(W, H), "gpu_launches": launches,
+        "data": "synthetic", "config": workload_config(W, H, a.streams), "gpu_launches": launches,
         "stages_ms": stages,
+        "streams": a.streams,
+        "partitions": {"solve_partitions": part_info[0], "pixel_sms": part_info[1],
+                       "note": "single-image calls: solves on 16-SM green-context partitions, pixel passes on "
+                               "the remaining SMs; steps on different streams overlap"},
+        "single_stream": {"ms_per_step": ms_one / a.steps, "MP_per_s": mp / (ms_one / a.steps / 1e3)},
+        "latency_ms": lat,
         "stage_loop": {"ms_per_step": ms_staged / a.steps,
                        "note": "stages_ms come from a second timed loop of the same workload with CUDA events "
                                "around each stage; those events keep the kernels from overlapping"},
@@ -451,14 +497,17 @@ def main():
             di = [hr.to_device_aligned(im, f"cuda:{local}") for im in ims]
             do = [hr.aligned_empty(h2, w2, device=f"cuda:{local}") for _ in ims]
             c2 = hr.Context(hr.Params(), device=local)
+            c2.set_tuning(partitions=3)  # smaller images: three 16-SM solve partitions (measured best below 8K)
             c3 = hr.Context(hr.Params(stage_timing=True), device=local)
             st = max(50, a.steps // 4)
-            mt, _, _ = timed_loop(c2, di, do, st, max(3, a.warmup // 2), None, torch)
+            mt, _, _ = timed_loop(c2, di, do, st, max(3, a.warmup // 2), None, torch, n_streams=a.streams)
+            m1, _, _ = timed_loop(c2, di, do, st, max(3, a.warmup // 2), None, torch)
             _, _, stg = timed_loop(c3, di, do, st, max(3, a.warmup // 2), None, torch, staged=True)
             c3.close()
             ms2 = mt / st
             rl = (2 * 3 * w2 * h2 + 3 * w2 * h2) / (pk["hbm_gbs"] * 1e9) * 1e3
             per[f"{w2}x{h2}"] = {"MP_per_s": w2 * h2 / 1e6 / (ms2 / 1000), "ms_per_image": ms2,
+                                 "streams": a.streams, "solve_partitions": 3, "single_stream_ms_per_image": m1 / st,
                                  "stages_ms": {"hist": stg[0], "solve": stg[1], "apply": stg[2]},
                                  "roofline_frac": rl / ms2}
             c2.close()

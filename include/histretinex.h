@@ -66,9 +66,20 @@ typedef enum {
 } hr_precision;
 
 enum {
-  HR_FLAG_FIXED_ITERS = 1u, /* always run max_iter iterations of Algorithm 1 (ignore eps) */
-  HR_FLAG_DEBUG_OUT = 2u,   /* keep per-image intermediates for histretinex_get_debug() */
-  HR_FLAG_STAGE_TIMING = 4u /* record CUDA events around each pipeline stage (histretinex_stage_times) */
+  HR_FLAG_FIXED_ITERS = 1u,  /* always run max_iter iterations of Algorithm 1 (ignore eps) */
+  HR_FLAG_DEBUG_OUT = 2u,    /* keep per-image intermediates for histretinex_get_debug() */
+  HR_FLAG_STAGE_TIMING = 4u, /* record CUDA events around each pipeline stage (histretinex_stage_times) */
+  /* Printed forms of three points the default readings settle otherwise (each may be set alone): */
+  HR_FLAG_PRINTED_UPDATE = 8u,    /* Eq. 12 and Eq. 13 as printed: the weight K_ij of Eq. 11 divides the
+                                     data term, sum_i H_C(R)_i H_C(S)_idx(i,j) / (N K_ij), instead of
+                                     multiplying it (the default is the stationary point of Eq. 10);
+                                     FP64 only (other precisions: HR_ERR_UNSUPPORTED at create) */
+  HR_FLAG_NEAREST_MATCH = 16u,    /* histogram matching (Sec. III.C) to the target level whose cumulative
+                                     share is nearest to the source level's: LUT[s] = first z minimising
+                                     |CT(z) N - CS(s) CT(K-1)| (default: the first z that reaches it) */
+  HR_FLAG_FORWARD_GRADIENT = 32u  /* the gradient image (Sec. III.B, Algorithm 1) by forward differences
+                                     gx = V(x+1,y) - V(x,y), gy = V(x,y+1) - V(x,y), replicate border
+                                     (default: the 3x3 Sobel operator); runs the generic histogram kernel */
 };
 
 /* Method parameters.  alpha, beta: weights of the illumination and reflectance priors
@@ -104,7 +115,14 @@ typedef struct hr_ctx hr_ctx;
  * GB300 (its cluster is placed while the histogram pass drains).  groups: a graph-replayed batch
  * of at least 64 images runs as 1 or 2 groups (default 2: images [0, n/2) and [n/2, n) on two
  * streams, the second group's histogram pass after the first's, so one group's solve overlaps the
- * other's pixel passes). */
+ * other's pixel passes).  partitions: 0, or the number (1..4) of 16-SM partitions the GPU's SMs are
+ * split into for the solves of single-image calls, the remaining SMs forming one partition for their
+ * pixel passes (green contexts; default 2).  A call then runs its histogram and apply passes in the
+ * pixel partition and its solve in the next solve partition, on the context's own streams, forked
+ * from and joined back into the caller's stream; calls on different caller streams overlap (one
+ * image's solve beside other images' pixel passes), with results bit-identical to partitions = 0.
+ * Single-image calls then use a ring of four workspace slots, each call the next.  Calls under
+ * stream capture or with stage timing, and devices whose SMs cannot be split so, run unpartitioned. */
 typedef struct {
   int hist_ctas_per_sm;
   int apply_ctas_per_sm;
@@ -112,6 +130,7 @@ typedef struct {
   int use_graph;
   int pdl;
   int groups;
+  int partitions;
 } hr_tuning;
 
 /* Fills *p with the defaults: K = 256, alpha = beta = 1e-3, gamma = 2.2 (Sec. III.C),
@@ -120,15 +139,22 @@ void histretinex_default_params(hr_params* p);
 
 /* Creates a context on `device` for parameters *p (copied).  Builds the per-K tables
  * (the Eq. 19 class map as per-row class boundaries).  Returns HR_ERR_INVALID_ARG for
- * invalid parameters, HR_ERR_CUDA / HR_ERR_OOM on device failures. */
+ * invalid parameters, HR_ERR_UNSUPPORTED for HR_FLAG_PRINTED_UPDATE with a precision other
+ * than FP64, HR_ERR_CUDA / HR_ERR_OOM on device failures. */
 hr_status histretinex_create(hr_ctx** out, const hr_params* p, int device);
 
 /* Enhances one image already in device memory (Sec. III, the whole pipeline above).
  * d_in, d_out: device pointers to W x H interleaved RGB images (may alias);
  * in_pitch, out_pitch: row strides in bytes; elem_bytes: 1 or 2.
- * Asynchronous on `stream`; the context's workspace is reused by the next call on any
- * stream, so calls on one context must be ordered (same stream or synchronised).
- * Images with W*H >= 2^31 return HR_ERR_UNSUPPORTED. */
+ * Asynchronous on `stream`: the call reads its input after the stream's earlier work and its
+ * output is complete when the stream reaches the work queued after it.  Calls on different
+ * streams may overlap on the device: each takes the next of the context's four single-image
+ * workspace slots and its device work waits for that slot's previous call, so such calls need no
+ * ordering by the caller (with SM partitions, hr_tuning.partitions > 0, one call's solve then runs
+ * beside other calls' pixel passes).  Under stream capture a call uses the context's first batch
+ * slot instead and orders nothing across streams: calls captured on different streams must be
+ * ordered by the caller.  A context must not be used from two host threads at once.  Images with
+ * W*H >= 2^31 return HR_ERR_UNSUPPORTED. */
 hr_status histretinex_enhance(hr_ctx* ctx, const void* d_in, void* d_out, int width, int height,
                               size_t in_pitch, size_t out_pitch, int elem_bytes, void* stream);
 
@@ -238,6 +264,12 @@ hr_status histretinex_profile_solve(hr_ctx* ctx, int image, long long* ns, int* 
  * of two in [8, 4096] (or above 256 for forms 0 and 1), m2_first < 0, n < 1, a null d_out or a
  * range beyond the form's; HR_ERR_CUDA if the launch fails. */
 hr_status histretinex_gradient_levels(int form, int K, int m2_first, int n, uint16_t* d_out, void* stream);
+
+/* The SM partitioning single-image calls run with (see hr_tuning.partitions): *solve_parts = the
+ * number of 16-SM solve partitions in use (0: unpartitioned, before the first call or where the
+ * split is unavailable), *pixel_sms = the SMs of the pixel partition (all SMs when unpartitioned).
+ * Not part of the paper's method. */
+hr_status histretinex_partition_info(const hr_ctx* ctx, int* solve_parts, int* pixel_sms);
 
 /* Number of kernels this library launched on the context since creation (for
  * launch accounting by callers and benchmarks). */

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libhistretinex.so")
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_RANGE, ERR_TIMEOUT = range(7)
 PREC_FP64, PREC_FP32, PREC_DF64 = 0, 1, 4
 FLAG_FIXED_ITERS, FLAG_DEBUG_OUT, FLAG_STAGE_TIMING = 1, 2, 4
+FLAG_PRINTED_UPDATE, FLAG_NEAREST_MATCH, FLAG_FORWARD_GRADIENT = 8, 16, 32
 
 # Every symbol include/histretinex.h declares.
 EXPORTS = (
@@ -25,7 +26,7 @@ EXPORTS = (
     "histretinex_status_string", "histretinex_kernel_launches", "histretinex_stage_times",
     "histretinex_profile_solve", "histretinex_set_tuning", "histretinex_get_tuning",
     "histretinex_workspace_bytes", "histretinex_enhance_noalloc", "histretinex_reserve",
-    "histretinex_enhance_host_many", "histretinex_gradient_levels",
+    "histretinex_enhance_host_many", "histretinex_gradient_levels", "histretinex_partition_info",
 )
 
 
@@ -50,6 +51,7 @@ class hr_tuning(ctypes.Structure):
         ("use_graph", ctypes.c_int),
         ("pdl", ctypes.c_int),
         ("groups", ctypes.c_int),
+        ("partitions", ctypes.c_int),
     ]
 
 
@@ -101,6 +103,8 @@ def _lib():
         L.histretinex_enhance_noalloc.restype = ctypes.c_int
         L.histretinex_reserve.argtypes = [vp, i]
         L.histretinex_reserve.restype = ctypes.c_int
+        L.histretinex_partition_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.histretinex_partition_info.restype = ctypes.c_int
         L.histretinex_gradient_levels.argtypes = [i, i, i, i, vp, vp]
         L.histretinex_gradient_levels.restype = ctypes.c_int
         L.histretinex_workspace_bytes.argtypes = [vp]
@@ -131,10 +135,14 @@ class Params:
     fixed_iters: bool = True
     debug: bool = False
     stage_timing: bool = False
+    printed_update: bool = False    # Eq. 12 / Eq. 13 as printed (the weight K_ij divides)
+    nearest_match: bool = False     # matching to the nearest cumulative share
+    forward_gradient: bool = False  # gradient image by forward differences
 
     def c(self) -> hr_params:
         flags = (FLAG_FIXED_ITERS if self.fixed_iters else 0) | (FLAG_DEBUG_OUT if self.debug else 0) | \
-            (FLAG_STAGE_TIMING if self.stage_timing else 0)
+            (FLAG_STAGE_TIMING if self.stage_timing else 0) | (FLAG_PRINTED_UPDATE if self.printed_update else 0) | \
+            (FLAG_NEAREST_MATCH if self.nearest_match else 0) | (FLAG_FORWARD_GRADIENT if self.forward_gradient else 0)
         return hr_params(self.K, self.alpha, self.beta, self.gamma, self.eps, self.max_iter, self.precision, flags)
 
 
@@ -353,7 +361,8 @@ class Context:
     def set_tuning(self, **kw):
         """Changes launch shapes (histretinex_set_tuning; fields as in hr_tuning): hist_ctas_per_sm,
         apply_ctas_per_sm (1..32), solve_cluster (1, 2, 4, 8, 16), use_graph (0/1), pdl (mask 0..7 of
-        the kernels launched as programmatic dependent launches), groups (1/2 for large batches).
+        the kernels launched as programmatic dependent launches), groups (1/2 for large batches),
+        partitions (0..4 solve partitions of 16 SMs for single-image calls).
         Fields not given keep their current values; invalid values raise and change nothing."""
         cur = self.tuning()
         cur.update(kw)
@@ -370,6 +379,13 @@ class Context:
     def reserve(self, n_images: int) -> None:
         """Allocates the workspace for batches of up to n_images now (later calls then allocate nothing)."""
         _check(_lib().histretinex_reserve(self._h, int(n_images)), "histretinex_reserve")
+
+    def partition_info(self):
+        """(solve partitions in use, SMs of the pixel partition) of single-image calls."""
+        a, b = ctypes.c_int(0), ctypes.c_int(0)
+        _check(_lib().histretinex_partition_info(self._h, ctypes.byref(a), ctypes.byref(b)),
+               "histretinex_partition_info")
+        return a.value, b.value
 
     def kernel_launches(self) -> int:
         return int(_lib().histretinex_kernel_launches(self._h))

@@ -47,15 +47,26 @@ struct hr_ctx {
   int ev_next = 0;
   double stage_ms[3] = {0, 0, 0};
   int stage_calls = 0;
-  hr_tuning tune{8, 16, 16, 1, 5, 2};
+  hr_tuning tune{8, 16, 16, 1, 5, 2, 2};
   // leading slots whose H_C(S) and H_C(grad S) are known to be zero (the solve clears them after
   // use unless the intermediates are kept for histretinex_get_debug)
   int hist_clean = 0;
   // captured batch pipeline and the geometry it was captured for
   cudaGraphExec_t graph = nullptr;
   int g_n = 0, g_total = 0, g_eb = 0, g_fast_in = 0, g_fast_out = 0, g_zero = 0, g_groups = 0, g_launches = 0;
-  hr_tuning g_tune{0, 0, 0, 0, 0, 0};
+  hr_tuning g_tune{0, 0, 0, 0, 0, 0, 0};
   int last_groups = 0;  // groups of the uploaded tables
+  // single-image calls on SM partitions: a ring of workspace slots, each known clean or not
+  static constexpr int kRingSlots = 4;
+  hr::Partitions* part = nullptr;
+  int part_parts = 0;               // partitions the current Partitions object was made with
+  bool part_unavailable = false;    // the split failed on this device: run unpartitioned
+  uint8_t* d_ring = nullptr;
+  bool ring_clean[kRingSlots] = {};
+  cudaEvent_t ring_free[kRingSlots] = {};  // recorded on the caller's stream after the slot's last call
+  bool ring_pending[kRingSlots] = {};
+  int ring_next = 0;
+  const uint8_t* last_base = nullptr;  // slot 0 of the last call's images (debug reads)
 };
 
 namespace hr {
@@ -70,6 +81,9 @@ hr_status check_params(const hr_params* p) {
   if (p->max_iter < 1) return HR_ERR_INVALID_ARG;
   if (p->precision != HR_PREC_FP64 && p->precision != HR_PREC_FP32 && p->precision != HR_PREC_DF64)
     return HR_ERR_INVALID_ARG;
+  // the printed update's values (S_k P_k, up to about N^3 / K, and reflectance bins that shrink
+  // towards zero) leave FP32's exponent range, which the FP32 and double-float forms share
+  if ((p->flags & HR_FLAG_PRINTED_UPDATE) && p->precision != HR_PREC_FP64) return HR_ERR_UNSUPPORTED;
   return HR_OK;
 }
 
@@ -221,6 +235,44 @@ struct Group {
   const int* order;  // (nullptr for one image)
 };
 
+// Arguments of the solve kernel for the images of group g.
+hr::SolveArgs solve_args(const hr_ctx* c, const Group& g) {
+  const bool debug = (c->p.flags & HR_FLAG_DEBUG_OUT) != 0;
+  hr::SolveArgs a{};
+  a.K = c->p.K;
+  a.alpha = c->p.alpha;
+  a.beta = c->p.beta;
+  a.eps = c->p.eps;
+  a.max_iter = c->p.max_iter;
+  a.fixed_iters = (c->p.flags & HR_FLAG_FIXED_ITERS) ? 1 : 0;
+  a.jstart1 = c->d_jstart1;
+  a.slots = g.slots;
+  a.order = g.order;
+  a.slot_bytes = c->lay.bytes;
+  a.lay = c->lay;
+  a.status = c->d_status;
+  a.profile = debug ? 1 : 0;
+  a.zero_hist = debug ? 0 : 1;
+  a.printed = (c->p.flags & HR_FLAG_PRINTED_UPDATE) ? 1 : 0;
+  a.nearest = (c->p.flags & HR_FLAG_NEAREST_MATCH) ? 1 : 0;
+  a.arith = c->p.precision == HR_PREC_FP32 ? hr::kArithF32 : (c->p.precision == HR_PREC_DF64 ? hr::kArithDF64 : hr::kArithF64);
+  return a;
+}
+
+// CTAs per image of the solve: the tuned cluster for one image; for a batch as many as keep all
+// images in one wave (the largest power of two with n C <= SMs, at most the tuned cluster), so a
+// batch of a few images runs as fast as its images would alone and a large one on one CTA each.
+int solve_ctas(const hr_ctx* c, int n, bool batched) {
+  int C = c->tune.solve_cluster;
+  if (batched) {
+    const int per = c->sm_count / n;
+    int p2 = 1;
+    while (2 * p2 <= per) p2 *= 2;
+    C = p2 < C ? p2 : C;
+  }
+  return C;
+}
+
 // The pipeline's device work for one group on one stream: zero the histograms (unless the previous
 // solves left them zero), histogram pass, solve, apply.  ev (optional): four events recorded around
 // the three stages; after_hist (optional): recorded after the histogram pass.
@@ -238,38 +290,14 @@ cudaError_t enqueue_stages(hr_ctx* c, const Group& g, int elem_bytes, bool fast_
   }
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
   e = hr::launch_hist(g.tab, g.total, g.units, g.interior, elem_bytes, K, g.slots, c->lay.bytes, c->lay, c->d_status,
-                      c->sm_count, c->tune.hist_ctas_per_sm, st, fast_in, (pdl & 1) != 0);
+                      c->sm_count, c->tune.hist_ctas_per_sm, st, fast_in, (pdl & 1) != 0,
+                      (c->p.flags & HR_FLAG_FORWARD_GRADIENT) != 0);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
   if (after_hist && (e = cudaEventRecord(after_hist, st)) != cudaSuccess) return e;
-  hr::SolveArgs a{};
-  a.K = K;
-  a.alpha = c->p.alpha;
-  a.beta = c->p.beta;
-  a.eps = c->p.eps;
-  a.max_iter = c->p.max_iter;
-  a.fixed_iters = (c->p.flags & HR_FLAG_FIXED_ITERS) ? 1 : 0;
-  a.jstart1 = c->d_jstart1;
-  a.slots = g.slots;
-  a.order = g.order;
-  a.slot_bytes = c->lay.bytes;
-  a.lay = c->lay;
-  a.status = c->d_status;
-  a.profile = debug ? 1 : 0;
-  a.zero_hist = debug ? 0 : 1;
-  a.arith = c->p.precision == HR_PREC_FP32 ? hr::kArithF32 : (c->p.precision == HR_PREC_DF64 ? hr::kArithDF64 : hr::kArithF64);
-  // CTAs per image: the tuned cluster for one image; for a batch as many as keep all images in
-  // one wave (the largest power of two with n C <= SMs, at most the tuned cluster), so a batch
-  // of a few images runs as fast as its images would alone and a large one on one CTA each
+  const hr::SolveArgs a = solve_args(c, g);
   *launches += 3;
-  int C = c->tune.solve_cluster;
-  if (batched) {
-    const int per = c->sm_count / n;
-    int p2 = 1;
-    while (2 * p2 <= per) p2 *= 2;
-    C = p2 < C ? p2 : C;
-  }
-  e = hr::launch_solve(a, n, C, st, (pdl & 2) != 0);
+  e = hr::launch_solve(a, n, solve_ctas(c, n, batched), st, (pdl & 2) != 0);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
   e = hr::launch_apply(g.tab, g.total, elem_bytes, K, g.slots, c->lay.bytes, c->lay, c->d_status, c->sm_count,
@@ -284,6 +312,122 @@ cudaError_t enqueue_stages(hr_ctx* c, const Group& g, int elem_bytes, bool fast_
 void note_hist_state(hr_ctx* c, int n, bool ok) {
   if (!ok || (c->p.flags & HR_FLAG_DEBUG_OUT)) c->hist_clean = 0;
   else if (n > c->hist_clean) c->hist_clean = n;
+}
+
+// Single-image calls take the slots of a ring in turn.  A call first makes its stream wait until
+// the slot's previous call (on whatever stream) is done, and marks the slot's release on its own
+// stream after its last kernel, so calls on different streams may overlap on the device.
+hr_status ring_acquire(hr_ctx* c, cudaStream_t st, int* r) {
+  if (!c->d_ring) {
+    HR_CUDA(cudaMalloc(&c->d_ring, c->lay.bytes * (size_t)hr_ctx::kRingSlots));
+    for (int i = 0; i < hr_ctx::kRingSlots; ++i) {
+      c->ring_clean[i] = false;
+      c->ring_pending[i] = false;
+      if (!c->ring_free[i]) HR_CUDA(cudaEventCreateWithFlags(&c->ring_free[i], cudaEventDisableTiming));
+    }
+  }
+  *r = c->ring_next;
+  c->ring_next = (*r + 1) % hr_ctx::kRingSlots;
+  if (c->ring_pending[*r]) HR_CUDA(cudaStreamWaitEvent(st, c->ring_free[*r], 0));
+  return HR_OK;
+}
+
+hr_status ring_release(hr_ctx* c, cudaStream_t st, int r) {
+  HR_CUDA(cudaEventRecord(c->ring_free[r], st));
+  c->ring_pending[r] = true;
+  return HR_OK;
+}
+
+bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) { cudaGetLastError(); return true; }
+  return cap != cudaStreamCaptureStatusNone;
+}
+
+// One image on the caller's stream in a ring slot (unpartitioned).
+hr_status run_ring(hr_ctx* c, const ImageDesc& d, int elem_bytes, bool fast_in, bool fast_out, cudaStream_t st,
+                   cudaEvent_t* ev) {
+  int r = 0;
+  hr_status s = ring_acquire(c, st, &r);
+  if (s != HR_OK) return s;
+  const bool debug = (c->p.flags & HR_FLAG_DEBUG_OUT) != 0;
+  Group g{};
+  g.tab.n = 1;
+  g.tab.one = d;
+  g.total = hr::tiles_of(d.W, d.H);
+  g.units = hr::strips_of(d.W, d.H);
+  g.interior = hr::interior_strips_of(d.W, d.H);
+  g.slots = c->d_ring + (size_t)r * c->lay.bytes;
+  g.order = nullptr;
+  int nl = 0;
+  const cudaError_t e = enqueue_stages(c, g, elem_bytes, fast_in, fast_out, false, debug || !c->ring_clean[r], st, ev, &nl);
+  c->ring_clean[r] = e == cudaSuccess && !debug;
+  if (e != cudaSuccess) return cuda_fail(e);
+  s = ring_release(c, st, r);
+  if (s != HR_OK) return s;
+  c->launches += (uint64_t)nl;
+  c->last_n = 1;
+  c->last_base = g.slots;
+  return HR_OK;
+}
+
+// One image on the SM partitions (sets *done); returns with *done false where the call runs
+// unpartitioned instead: under stream capture, or when the device's SMs cannot be split.
+hr_status run_partitioned(hr_ctx* c, const ImageDesc& d, int elem_bytes, bool fast_in, bool fast_out,
+                          cudaStream_t st, bool* done) {
+  *done = false;
+  if (c->part_unavailable) return HR_OK;
+  if (c->part && c->part_parts != c->tune.partitions) {
+    hr::partitions_destroy(c->part);  // (synchronises the partitions' streams)
+    c->part = nullptr;
+  }
+  if (!c->part) {
+    const hr_status ps = hr::partitions_create(c->device, c->tune.partitions, hr_ctx::kRingSlots, &c->part);
+    if (ps == HR_ERR_UNSUPPORTED) { c->part_unavailable = true; return HR_OK; }
+    if (ps != HR_OK) return ps;
+    c->part_parts = c->tune.partitions;
+  }
+  int r = 0;
+  hr_status rs = ring_acquire(c, st, &r);
+  if (rs != HR_OK) return rs;
+  const int K = c->p.K;
+  const bool debug = (c->p.flags & HR_FLAG_DEBUG_OUT) != 0;
+  const bool zero = debug || !c->ring_clean[r];
+  const int sms = hr::partitions_pixel_sms(c->part);
+  Group g{};
+  g.tab.n = 1;
+  g.tab.one = d;
+  g.total = hr::tiles_of(d.W, d.H);
+  g.units = hr::strips_of(d.W, d.H);
+  g.interior = hr::interior_strips_of(d.W, d.H);
+  g.slots = c->d_ring + (size_t)r * c->lay.bytes;
+  g.order = nullptr;
+  const hr::SolveArgs a = solve_args(c, g);
+  const bool forward = (c->p.flags & HR_FLAG_FORWARD_GRADIENT) != 0;
+  // (no programmatic dependent launches: each pixel pass follows an event wait on its stream)
+  auto hist = [&](cudaStream_t s) {
+    if (zero) {
+      const cudaError_t e = cudaMemsetAsync(g.slots + c->lay.S, 0, (size_t)2 * K * sizeof(unsigned), s);
+      if (e != cudaSuccess) return e;
+    }
+    return hr::launch_hist(g.tab, g.total, g.units, g.interior, elem_bytes, K, g.slots, c->lay.bytes, c->lay,
+                           c->d_status, sms, c->tune.hist_ctas_per_sm, s, fast_in, false, forward);
+  };
+  auto solve = [&](cudaStream_t s) { return hr::launch_solve(a, 1, solve_ctas(c, 1, false), s, false); };
+  auto apply = [&](cudaStream_t s) {
+    return hr::launch_apply(g.tab, g.total, elem_bytes, K, g.slots, c->lay.bytes, c->lay, c->d_status, sms,
+                            c->tune.apply_ctas_per_sm, s, fast_out, false);
+  };
+  const cudaError_t e = hr::partitions_run(c->part, r, st, hist, solve, apply);
+  c->ring_clean[r] = e == cudaSuccess && !debug;
+  if (e != cudaSuccess) return cuda_fail(e);
+  rs = ring_release(c, st, r);
+  if (rs != HR_OK) return rs;
+  *done = true;
+  c->launches += 3;
+  c->last_n = 1;
+  c->last_base = g.slots;
+  return HR_OK;
 }
 
 hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, cudaStream_t st, bool batched) {
@@ -310,10 +454,18 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
     fast_in = fast_in && ain;
     fast_out = fast_out && ain && aout;
   }
-  hr_status s = ensure_slots(c, n);
-  if (s != HR_OK) return s;
   const bool debug = (c->p.flags & HR_FLAG_DEBUG_OUT) != 0;
   const bool timing = (c->p.flags & HR_FLAG_STAGE_TIMING) != 0;
+  // single images: the ring of slots (on the SM partitions unless timing or disabled), except under
+  // stream capture, where a call keeps to batch slot 0 and orders nothing across streams
+  const bool ring = n == 1 && !batched && !capturing(st);
+  if (ring && !timing && c->tune.partitions > 0) {
+    bool partitioned = false;
+    hr_status ps = run_partitioned(c, imgs[0], elem_bytes, fast_in, fast_out, st, &partitioned);
+    if (partitioned || ps != HR_OK) return ps;
+  }
+  hr_status s = ensure_slots(c, n);
+  if (s != HR_OK) return s;
   const bool graph = batched && c->tune.use_graph && n > 1 && !timing;
   // A large graph-replayed batch may run as two groups (images [0, n/2) and [n/2, n)) on two
   // streams, the second group's histogram pass after the first's, so that one group's solve
@@ -436,6 +588,7 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
     if (e != cudaSuccess) return cuda_fail(e);
     c->launches += (uint64_t)c->g_launches;
     c->last_n = n;
+    c->last_base = c->d_slots;
     return HR_OK;
   }
   cudaEvent_t* ev = nullptr;
@@ -449,6 +602,7 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
     ev = c->ev[i];
     c->ev_used[i] = true;
   }
+  if (ring) return run_ring(c, imgs[0], elem_bytes, fast_in, fast_out, st, ev);
   const bool zero = debug || c->hist_clean < n;
   int nl = 0;
   const cudaError_t e = enqueue_stages(c, grp[0], elem_bytes, fast_in, fast_out, batched, zero, st, ev, &nl);
@@ -456,6 +610,7 @@ hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, 
   if (e != cudaSuccess) return cuda_fail(e);
   c->launches += (uint64_t)nl;
   c->last_n = n;
+  c->last_base = c->d_slots;
   return HR_OK;
 }
 
@@ -639,7 +794,7 @@ hr_status histretinex_get_debug(hr_ctx* c, int image, uint64_t* S, uint64_t* G, 
   HR_CUDA(cudaSetDevice(c->device));
   HR_CUDA(cudaDeviceSynchronize());
   const int K = c->p.K;
-  const uint8_t* slot = c->d_slots + (size_t)image * c->lay.bytes;
+  const uint8_t* slot = c->last_base + (size_t)image * c->lay.bytes;
   std::vector<unsigned> tmp((size_t)K);
   if (S) {
     HR_CUDA(cudaMemcpy(tmp.data(), slot + c->lay.S, (size_t)K * 4, cudaMemcpyDeviceToHost));
@@ -667,7 +822,7 @@ hr_status histretinex_profile_solve(hr_ctx* c, int image, long long* ns, int* co
   HR_CUDA(cudaSetDevice(c->device));
   HR_CUDA(cudaDeviceSynchronize());
   long long buf[hr::kProfSlots];
-  HR_CUDA(cudaMemcpy(buf, c->d_slots + (size_t)image * c->lay.bytes + c->lay.misc + 16, sizeof(buf),
+  HR_CUDA(cudaMemcpy(buf, c->last_base + (size_t)image * c->lay.bytes + c->lay.misc + 16, sizeof(buf),
                      cudaMemcpyDeviceToHost));
   int n = 0;
   while (n < hr::kProfSlots && buf[n] != 0) ++n;
@@ -694,6 +849,10 @@ hr_status histretinex_destroy(hr_ctx* c) {
   if (!c) return HR_OK;
   cudaSetDevice(c->device);
   if (c->desc_done) cudaEventSynchronize(c->desc_done);
+  hr::partitions_destroy(c->part);
+  cudaFree(c->d_ring);
+  for (int i = 0; i < hr_ctx::kRingSlots; ++i)
+    if (c->ring_free[i]) cudaEventDestroy(c->ring_free[i]);
   cudaFree(c->d_slots);
   cudaFree(c->d_jstart1);
   cudaFree(c->d_status);
@@ -754,6 +913,7 @@ hr_status histretinex_set_tuning(hr_ctx* c, const hr_tuning* t) {
   if (t->use_graph != 0 && t->use_graph != 1) return HR_ERR_INVALID_ARG;
   if (t->pdl < 0 || t->pdl > 7) return HR_ERR_INVALID_ARG;
   if (t->groups != 1 && t->groups != 2) return HR_ERR_INVALID_ARG;
+  if (t->partitions < 0 || t->partitions > 4) return HR_ERR_INVALID_ARG;
   c->tune = *t;
   return HR_OK;
 }
@@ -782,6 +942,14 @@ hr_status histretinex_stage_times(hr_ctx* c, double* ms, int* calls, int reset) 
 }
 
 uint64_t histretinex_kernel_launches(const hr_ctx* c) { return c ? c->launches : 0; }
+
+hr_status histretinex_partition_info(const hr_ctx* c, int* solve_parts, int* pixel_sms) {
+  if (!c || !solve_parts || !pixel_sms) return HR_ERR_INVALID_ARG;
+  const bool on = c->part && c->tune.partitions == c->part_parts;  // (a changed count applies at the next call)
+  *solve_parts = on ? c->part_parts : 0;
+  *pixel_sms = on ? hr::partitions_pixel_sms(c->part) : c->sm_count;
+  return HR_OK;
+}
 
 hr_status histretinex_gradient_levels(int form, int K, int m2_first, int n, uint16_t* d_out, void* stream) {
   if (form < 0 || form > 2 || !hr::pow2(K) || K < 8 || K > 4096 || m2_first < 0 || n < 1 || !d_out)

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <cuda_runtime.h>
 
 #include "../../include/histretinex.h"
@@ -118,6 +119,8 @@ struct SolveArgs {
   int profile;               // 1: record phase timestamps into the slot's misc area
   int arith;                 // kArithF64 (plain form), kArithF32 (reduced precision), kArithDF64
   int zero_hist;             // 1: clear H_C(S) and H_C(grad S) after use, ready for the next call
+  int printed;               // 1: Eq. 12 / Eq. 13 as printed (the weight K_ij divides)
+  int nearest;               // 1: matching to the nearest cumulative share
 };
 
 // Launchers (return cudaError_t of the launch).  pdl: programmatic dependent launch (the kernel
@@ -127,10 +130,11 @@ struct SolveArgs {
 // strip list (kStripW x kBandH units); both lists are given, with their totals and the number of
 // interior strips (strips that cross no right or bottom image edge).  Tile kernels
 // run sms x ctas_per_sm CTAs, the strip kernel one CTA per SM.
+// forward: the gradient image by forward differences (generic kernel) instead of the Sobel operator.
 cudaError_t launch_hist(const ImgTab& tab, int total_tiles, int total_units, int interior_units, int elem_bytes,
                         int K, uint8_t* slots,
                         size_t slot_bytes, SlotLayout lay, unsigned* status, int sms, int ctas_per_sm,
-                        cudaStream_t st, bool fast, bool pdl);
+                        cudaStream_t st, bool fast, bool pdl, bool forward = false);
 cudaError_t launch_solve(const SolveArgs& a, int n, int cluster, cudaStream_t st, bool pdl);
 cudaError_t launch_apply(const ImgTab& tab, int total_tiles, int elem_bytes, int K, uint8_t* slots, size_t slot_bytes,
                          SlotLayout lay, unsigned* status, int sms, int ctas_per_sm, cudaStream_t st, bool fast,
@@ -139,6 +143,20 @@ cudaError_t launch_apply(const ImgTab& tab, int total_tiles, int elem_bytes, int
 // three device forms (0: strip kernel, 1: staged-tile kernel, 2: generic kernel), into out[n].
 cudaError_t launch_grad_level_probe(int form, int K, int m2_first, int n, uint16_t* out, cudaStream_t st);
 size_t solve_smem_bytes(int K, int vec_in_smem, int list_in_smem, size_t fsize);
+
+// SM partitions for overlapping single-image calls (green contexts): `parts` partitions of 16 SMs
+// for solves and one of the remaining SMs for the pixel passes; `ring` pixel streams, one per
+// workspace slot.  partitions_run forks one call from the caller's stream st: hist on the slot's
+// pixel stream, solve on the next solve partition, apply back on the pixel stream, then st waits
+// for it.  Each StageFn enqueues its stage on the stream it is given (the partition's context is
+// current while it runs).
+using StageFn = std::function<cudaError_t(cudaStream_t)>;
+struct Partitions;
+hr_status partitions_create(int device, int parts, int ring, Partitions** out);
+void partitions_destroy(Partitions* P);
+int partitions_pixel_sms(const Partitions* P);
+cudaError_t partitions_run(Partitions* P, int slot, cudaStream_t st, const StageFn& hist, const StageFn& solve,
+                           const StageFn& apply);
 
 // Geometry of the pixel passes: tiles of kTileW x kTileH pixels.
 constexpr int kTileW = 128;

@@ -48,7 +48,7 @@ __device__ __forceinline__ unsigned round_sqrt(unsigned m2) {
 template <typename ET>
 __global__ void __launch_bounds__(kThreads) hist_kernel(const ImgTab tab, int total, int K,
                                                         uint8_t* slots, size_t slot_bytes, SlotLayout lay,
-                                                        unsigned* status) {
+                                                        unsigned* status, int forward) {
   pdl_wait();     // the previous kernel on the stream has finished
   pdl_trigger();  // the next one may be scheduled (it waits for this one)
   const int n = tab.n;
@@ -106,8 +106,10 @@ __global__ void __launch_bounds__(kThreads) hist_kernel(const ImgTab tab, int to
       const int a00 = p[-kVW - 1], a01 = p[-kVW], a02 = p[-kVW + 1];
       const int a10 = p[-1], a11 = p[0], a12 = p[1];
       const int a20 = p[kVW - 1], a21 = p[kVW], a22 = p[kVW + 1];
-      const int gx = (a02 + 2 * a12 + a22) - (a00 + 2 * a10 + a20);
-      const int gy = (a20 + 2 * a21 + a22) - (a00 + 2 * a01 + a02);
+      // 3x3 Sobel, or forward differences (the halo replicates the border, so both are zero at
+      // the last column and row)
+      const int gx = forward ? a12 - a11 : (a02 + 2 * a12 + a22) - (a00 + 2 * a10 + a20);
+      const int gy = forward ? a21 - a11 : (a20 + 2 * a21 + a22) - (a00 + 2 * a01 + a02);
       unsigned g = round_sqrt((unsigned)(gx * gx + gy * gy));
       g = g < (unsigned)(K - 1) ? g : (unsigned)(K - 1);
       atomicAdd(my_hs + a11, 1u);
@@ -881,8 +883,9 @@ cudaError_t launch_grad_level_probe(int form, int K, int m2_first, int n, uint16
 cudaError_t launch_hist(const ImgTab& tab, int total_tiles, int total_units, int interior_units, int elem_bytes,
                         int K, uint8_t* slots,
                         size_t slot_bytes, SlotLayout lay, unsigned* status, int sms, int ctas_per_sm,
-                        cudaStream_t st, bool fast, bool pdl) {
+                        cudaStream_t st, bool fast, bool pdl, bool forward) {
   const int copies = K <= 256 ? kWarps : 1;
+  if (forward) fast = false;  // the forward-difference gradient runs on the generic kernel
   const size_t smem = (size_t)2 * copies * K * sizeof(unsigned) + (size_t)kVH * kVW * sizeof(unsigned short);
   // strips when the launch has at least HR_STRIP_MIN_FACTOR of them per warp of a full grid (one
   // large image or a large batch), staged tiles otherwise
@@ -910,11 +913,11 @@ cudaError_t launch_hist(const ImgTab& tab, int total_tiles, int total_units, int
   if (elem_bytes == 1) {
     cudaFuncSetAttribute(hist_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return launch_kernel(hist_kernel<uint8_t>, dim3(grid), dim3(kThreads), smem, st, pdl, tab, total_tiles, K, slots,
-                         slot_bytes, lay, status);
+                         slot_bytes, lay, status, (int)forward);
   }
   cudaFuncSetAttribute(hist_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return launch_kernel(hist_kernel<uint16_t>, dim3(grid), dim3(kThreads), smem, st, pdl, tab, total_tiles, K, slots,
-                       slot_bytes, lay, status);
+                       slot_bytes, lay, status, (int)forward);
 }
 
 cudaError_t launch_apply(const ImgTab& tab, int total_tiles, int elem_bytes, int K, uint8_t* slots, size_t slot_bytes,

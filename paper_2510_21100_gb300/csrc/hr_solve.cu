@@ -648,14 +648,16 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         scal[0] = rcpF(fmaF(s2 * (sl * sl), invNN, beta));
       }  // (the second reciprocal needs the first: a chain)
     }
-    for (int b = tid; b < nL; b += NT) { const F x = L0[b]; L2c[b] = x * x; }
+    // row weights of the Eq. 13 sums: L^2 (stationary point of Eq. 10), 1 (Eq. 13 as printed)
+    for (int b = tid; b < nL; b += NT) { const F x = L0[b]; L2c[b] = A.printed ? (F)1.0 : x * x; }
     if (it == 1) stamp();
     class_totals<F>(PP, csz, pst, R0, L0, [&](int c, F Pu) { RRc[c] = Pu; });  // (R'R is free until Eq. 13)
     __syncthreads();
     for (int c = PP.cA + tid; c < PP.cB; c += NT) {  // q of all own classes together (scal[3] is set)
       const int k = LJ[c];
       const F P = RRc[c] * (scR * scal[3]);
-      q[k] = P > 0.0 ? Sd[k] * rcpF(P) : 0.0;
+      // q_k = S_k / P_k; as printed the weight K_ij = R_i L_j / P_k divides, so q_k = S_k P_k
+      q[k] = A.printed ? Sd[k] * P : (P > 0.0 ? Sd[k] * rcpF(P) : (F)0.0);
     }
     __syncthreads();
     if (it == 1) stamp();
@@ -667,7 +669,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
 
     // Eq. 13 for the own rows: lane groups of GA over the illumination bins.
     {
-      const F rdR = scal[0], sl2 = scL * scL;
+      const F rdR = scal[0], sl2 = A.printed ? (F)1.0 : scL * scL;
       const int gi = lane / GA, gl = lane % GA, rpw = 32 / GA;
       for (int a0 = aA + warp * rpw; a0 < aB; a0 += NW * rpw) {
         const int a = a0 + gi;
@@ -679,10 +681,12 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         }
         for (int o = GA >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
         if (gl == 0 && a < aB) {
+          // R'_i = ((R_i / N) sum_j L_j^2 q + beta G_i) / den; as printed ((1 / (N R_i)) sum_j S_k P_k + ...)
           const F r = scR * R0[a];
-          const F ru = fmaF(r * invN, acc * sl2, beta * (F)G[RI[a]]) * rdR;
+          const F rr = A.printed ? rcpF(r) : r;
+          const F ru = fmaF(A.printed ? invN * rr : r * invN, acc * sl2, beta * (F)G[RI[a]]) * rdR;
           R1[a] = ru;
-          RRc[a] = ru * r;
+          RRc[a] = ru * rr;  // column weight of Eq. 12: R'_i R_i, as printed R'_i / R_i
         }
       }
     }
@@ -725,7 +729,10 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
       __syncthreads();
       if (it == 1) stamp();
       const F rdL = scal[1];
-      for (int b = bA + tid; b < bB; b += NT) L1[b] = fmaF(scL * L0[b] * invN, Bs[b], alpha * Sd[LJ[b]]) * rdL;
+      for (int b = bA + tid; b < bB; b += NT) {
+        const F l = scL * L0[b];  // L'_j = ((L_j / N) B_j + alpha S_j) / den; as printed (B_j / (N L_j) + ...)
+        L1[b] = fmaF(A.printed ? invN * rcpF(l) : l * invN, Bs[b], alpha * Sd[LJ[b]]) * rdL;
+      }
     }
     __syncthreads();
     if (it == 1) stamp();
@@ -965,6 +972,29 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (lhs[mid] >= rhs) hi = mid; else lo = mid + 1;
+      }
+      if (A.nearest) {
+        // the first z minimising |CT(z) N - CS(s) TT|: lhs is monotone, so the minimum lies at lo or
+        // at the first z of the plateau just below it (the first of equal distances is the earlier)
+        const double r = __longlong_as_double((long long)rhs);
+        const double d1 = fabs(__longlong_as_double((long long)lhs[lo]) - r);
+        unsigned long long below = 0ull;
+        bool take_below = false;
+        if (lhs[lo] < rhs) {            // none reaches rhs: the nearest is the top plateau
+          below = lhs[lo];
+          take_below = true;
+        } else if (lo > 0) {
+          below = lhs[lo - 1];
+          take_below = r - __longlong_as_double((long long)below) <= d1;
+        }
+        if (take_below) {
+          int a = 0, b = lo;  // first z with lhs(z) >= below
+          while (a < b) {
+            const int mid = (a + b) >> 1;
+            if (lhs[mid] >= below) b = mid; else a = mid + 1;
+          }
+          lo = a;
+        }
       }
       lut[k] = (uint16_t)lo;
     }

@@ -134,7 +134,7 @@ extern "C" hr_status histretinex_enhance_noalloc(const hr_params* p, const void*
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return HR_ERR_CUDA;
   e = hr::launch_hist(tab, tiles, units, hr::interior_strips_of(width, height), elem_bytes, K, base, lay.bytes, lay,
-                      d_status, sms, 8, st, fast_in, true);
+                      d_status, sms, 8, st, fast_in, true, (p->flags & HR_FLAG_FORWARD_GRADIENT) != 0);
   if (e != cudaSuccess) return HR_ERR_CUDA;
   hr::SolveArgs a{};
   a.K = K;
@@ -149,6 +149,8 @@ extern "C" hr_status histretinex_enhance_noalloc(const hr_params* p, const void*
   a.lay = lay;
   a.status = d_status;
   a.profile = 0;
+  a.printed = (p->flags & HR_FLAG_PRINTED_UPDATE) ? 1 : 0;
+  a.nearest = (p->flags & HR_FLAG_NEAREST_MATCH) ? 1 : 0;
   a.arith = p->precision == HR_PREC_FP32 ? hr::kArithF32 : (p->precision == HR_PREC_DF64 ? hr::kArithDF64 : hr::kArithF64);
   e = hr::launch_solve(a, 1, 16, st, false);
   if (e != cudaSuccess) return HR_ERR_CUDA;

@@ -16,8 +16,10 @@ RTOL = 1e-9
 def params_pair(**kw):
     import paper_2510_21100_gb300 as hr
     p = hr.Params(**kw)
+    variants = (oracle.VAR_PRINTED_UPDATE if p.printed_update else 0) | \
+        (oracle.VAR_NEAREST_MATCH if p.nearest_match else 0) | (oracle.VAR_FORWARD_GRADIENT if p.forward_gradient else 0)
     po = oracle.Params(K=p.K, alpha=p.alpha, beta=p.beta, gamma=p.gamma, eps=p.eps, max_iter=p.max_iter,
-                       fixed_iters=p.fixed_iters)
+                       fixed_iters=p.fixed_iters, variants=variants)
     return p, po
 
 
