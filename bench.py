@@ -268,6 +268,30 @@ def precision_leg(torch, hr, local, n_imgs=1024, steps=2, warmup=1):
                                    "reference": "FP64 CPU oracle, same images"}}
 
 
+def gamma_leg(hr, local):
+    """The gamma-sensitivity study (Table III analogue) on a synthetic 1000x664 image through the
+    GPU path: PSNR / SSIM / LOE to the input, mean V, and PSNR / SSIM to the scene's normal-light
+    rendering, for gamma = 1, 1.5, 2.2, 5, 10."""
+    from paper_2510_21100_gb300 import quality, synth
+    W, H = 1000, 664
+    seed = synth.seed_for(6, 0)
+    img = synth.low_light_image(W, H, seed=seed)
+    ref = synth.normal_light_image(W, H, seed=seed)
+    d = hr.to_device_aligned(img, f"cuda:{local}")
+    rows = []
+    for g in (1.0, 1.5, 2.2, 5.0, 10.0):
+        with hr.Context(hr.Params(gamma=g, alpha=1e-4, beta=1e-4), device=local) as ctx:
+            out = ctx.enhance(d, hr.aligned_empty(H, W, device=f"cuda:{local}")).cpu().numpy()
+            ctx.check()
+        rows.append({"gamma": g, "psnr_input": round(quality.psnr(out, img), 4),
+                     "ssim_input": round(quality.ssim(out, img), 4), "loe": round(quality.loe(img, out), 3),
+                     "mean_V": round(quality.mean_value(out), 3), "psnr_reference": round(quality.psnr(out, ref), 4),
+                     "ssim_reference": round(quality.ssim(out, ref), 4)})
+    return {"workload": "synthetic 1000x664 uint8 low-light image (seed 6000000) and its normal-light rendering, "
+                        "K=256, T=10, alpha=beta=1e-4", "input_mean_V": round(quality.mean_value(img), 3),
+            "rows": rows}
+
+
 def serving_leg(torch, hr, local, big_img, seconds=5.0, rate=400.0, seed=5):
     """Continuous batching under Poisson arrivals (mean `rate` per second) of mixed-size 8-bit
     requests: 70% of 0.3-2 MP, 25% of 2-8 MP, 5% of 7680x4320; 40 GB device budget.  The request
@@ -518,6 +542,7 @@ def main():
         torch.cuda.empty_cache()  # the legs' device buffers go back before the latency-sensitive one
         line["serving"] = serving_leg(torch, hr, local, imgs[0])
         line["precision"] = precision_leg(torch, hr, local)
+        line["gamma_sensitivity"] = gamma_leg(hr, local)
         rate, reps, shape = cpu_oracle_rate(imgs, seconds=10.0)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{reps} x full {shape[1]}x{shape[0]} image, single-threaded FP64 C oracle"}

@@ -38,6 +38,7 @@ class _Params(ctypes.Structure):
         ("max_iter", ctypes.c_int),
         ("fixed_iters", ctypes.c_int),
         ("variants", ctypes.c_int),
+        ("levels", ctypes.c_int),
     ]
 
 
@@ -59,10 +60,11 @@ class Params:
     max_iter: int = 10
     fixed_iters: bool = True
     variants: int = 0
+    levels: int = 0   # M data levels binned into K bins (0: M = K)
 
     def c(self) -> _Params:
         return _Params(self.K, self.alpha, self.beta, self.gamma, self.eps, self.max_iter, int(self.fixed_iters),
-                       int(self.variants))
+                       int(self.variants), int(self.levels))
 
 
 def build(force: bool = False) -> str:
@@ -93,6 +95,14 @@ def lib():
         L.orc_iterate_v.argtypes = [vp, vp, i, d, d, i, vp, vp, vp, vp, vp, vp, vp, vp]
         L.orc_histograms_v.argtypes = [vp, i, i, sz, i, i, i, vp, vp]
         L.orc_lut_v.argtypes = [vp, vp, i, i, vp]
+        L.orc_histograms_b.argtypes = [vp, i, i, sz, i, i, i, i, vp, vp]
+        L.orc_bin_location.argtypes = [i, i, i]
+        L.orc_bin_location.restype = d
+        L.orc_class_table.argtypes = [i, i, vp]
+        L.orc_index1_table_b.argtypes = [i, i, d, vp]
+        L.orc_target_b.argtypes = [vp, vp, i, i, d, ctypes.c_uint64, vp]
+        L.orc_apply_b.argtypes = [vp, vp, i, i, sz, sz, i, i, i, vp]
+        L.orc_iterate_b.argtypes = [vp, vp, i, i, d, d, i, vp, vp, vp, vp, vp, vp, vp, vp]
         L.orc_solve.argtypes = [vp, vp, ctypes.POINTER(_Params), vp, vp, ctypes.POINTER(ctypes.c_int)]
         L.orc_index1_table.argtypes = [i, d, vp]
         L.orc_target.argtypes = [vp, vp, i, d, ctypes.c_uint64, vp]
@@ -235,3 +245,56 @@ def enhance(img: np.ndarray, p: Params) -> Result:
     _check(lib().orc_enhance(_ptr(img), _ptr(out), W, H, pitch, pitch, eb, ctypes.byref(cp), _ptr(S), _ptr(G),
                              _ptr(R), _ptr(L), _ptr(T), _ptr(lt), ctypes.byref(it)))
     return Result(out, S, G, R, L, T, lt, it.value)
+
+
+# ---- binned data: K bins over M data levels ----
+
+def histograms_binned(img: np.ndarray, K: int, M: int, forward: bool = False):
+    img, W, H, pitch, eb = _img_args(img)
+    S = np.zeros(K, dtype=np.uint64)
+    G = np.zeros(K, dtype=np.uint64)
+    _check(lib().orc_histograms_b(_ptr(img), W, H, pitch, eb, K, M, int(forward), _ptr(S), _ptr(G)))
+    return S, G
+
+
+def bin_location(k: int, K: int, M: int) -> float:
+    return float(lib().orc_bin_location(k, K, M))
+
+
+def class_table(K: int, M: int) -> np.ndarray:
+    t = np.zeros((K, K), dtype=np.uint32)
+    _check(lib().orc_class_table(K, M, _ptr(t)))
+    return t
+
+
+def index1_table_binned(K: int, M: int, gamma: float) -> np.ndarray:
+    t = np.zeros((K, K), dtype=np.uint32)
+    _check(lib().orc_index1_table_b(K, M, gamma, _ptr(t)))
+    return t
+
+
+def target_binned(R, L, K: int, M: int, gamma: float, N: int) -> np.ndarray:
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    T = np.zeros(K, dtype=np.float64)
+    _check(lib().orc_target_b(_ptr(R), _ptr(L), K, M, gamma, int(N), _ptr(T)))
+    return T
+
+
+def apply_binned(img: np.ndarray, lut_: np.ndarray, K: int, M: int) -> np.ndarray:
+    img, W, H, pitch, eb = _img_args(img)
+    lut_ = np.ascontiguousarray(lut_, dtype=np.uint16)
+    out = np.zeros_like(img)
+    _check(lib().orc_apply_b(_ptr(img), _ptr(out), W, H, pitch, pitch, eb, K, M, _ptr(lut_)))
+    return out
+
+
+def iterate_binned(S, G, R, L, K: int, M: int, alpha: float, beta: float, printed: bool = False):
+    S = np.ascontiguousarray(S, dtype=np.uint64)
+    G = np.ascontiguousarray(G, dtype=np.uint64)
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    out = {k: np.zeros(K, dtype=np.float64) for k in ("P", "q", "Ru", "Lu", "Rn", "Ln")}
+    _check(lib().orc_iterate_b(_ptr(S), _ptr(G), K, M, alpha, beta, int(printed), _ptr(R), _ptr(L), _ptr(out["P"]),
+                               _ptr(out["q"]), _ptr(out["Ru"]), _ptr(out["Lu"]), _ptr(out["Rn"]), _ptr(out["Ln"])))
+    return out

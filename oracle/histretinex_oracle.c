@@ -34,7 +34,11 @@
  *   - gradient = 3x3 Sobel magnitude of integer V, replicate border, rounded half up and
  *     clipped to K-1;
  *   - matching LUT[s] = smallest z with CT(z) * N >= CS(s) * CT(K-1);
- *   - colour: out_c = round_half_up(c * V'/V), and (V', V', V') where V = 0.
+ *   - colour: out_c = round_half_up(c * V'/V), and (V', V', V') where V = 0;
+ *   - binned data (K bins over M > K data levels, "l levels" of Sec. II): value v in bin
+ *     v >> log2(M/K); bin k located at its centre value, normalised, (k w + (w-1)/2) / (M-1)
+ *     (w = M/K); class maps as FP64 argmins over those locations; the gradient level clipped to
+ *     M-1 and binned likewise; the new value keeps the pixel's place in its bin.
  *
  * Canonical FP64 evaluation: every sum runs in ascending index order (cells of the K x K
  * matrices in row-major order, row = reflectance bin), one IEEE operation per written
@@ -60,6 +64,7 @@ typedef struct {
   int max_iter;     /* T of Algorithm 1 */
   int fixed_iters;  /* nonzero: always run max_iter iterations */
   int variants;     /* ORC_VAR_* bits: the printed forms instead of the default readings */
+  int levels;       /* M, the data's levels (a power of two >= K); 0 or K: one bin per level */
 } orc_params;
 
 /* Printed forms of three points the default readings settle otherwise (each selectable alone):
@@ -137,28 +142,80 @@ int orc_value_channel(const void* in, int W, int H, size_t pitch, int elem_bytes
   return bad ? ORC_ERR_RANGE : ORC_OK;
 }
 
-/* H_C(S) (Eq. 3) and H_C(grad S) (gradient histogram, Alg. 1 initialisation); forward selects
- * the forward-difference gradient (ORC_VAR_FORWARD_GRADIENT) instead of the Sobel operator. */
-int orc_histograms_v(const void* in, int W, int H, size_t pitch, int elem_bytes, int K, int forward, uint64_t* S,
-                     uint64_t* G) {
-  if (K < 2 || !S || !G) return ORC_ERR_INVALID_ARG;
+/* log2 of the bin width w = M / K (M, K powers of two, M >= K), or -1 if they do not qualify. */
+static int bin_shift(int K, int M) {
+  if (K < 2 || M < K || (K & (K - 1)) || (M & (M - 1))) return -1;
+  int s = 0;
+  while ((K << s) < M) ++s;
+  return s;
+}
+
+/* H_C(S) (Eq. 3) and H_C(grad S) (gradient histogram, Alg. 1 initialisation) over K bins of the
+ * data's M levels ("l levels", Sec. II preamble): a value v falls into bin v >> log2(M / K); the
+ * gradient level (clipped to the data's range, M - 1) is binned the same way.  M = K: one bin per
+ * level.  forward selects the forward-difference gradient (ORC_VAR_FORWARD_GRADIENT). */
+int orc_histograms_b(const void* in, int W, int H, size_t pitch, int elem_bytes, int K, int M, int forward,
+                     uint64_t* S, uint64_t* G) {
+  const int sh = bin_shift(K, M);
+  if (sh < 0 || !S || !G) return ORC_ERR_INVALID_ARG;
   unsigned* V = (unsigned*)malloc(sizeof(unsigned) * (size_t)W * (size_t)H);
   if (!V) return ORC_ERR_INVALID_ARG;
-  int st = orc_value_channel(in, W, H, pitch, elem_bytes, K, V);
+  int st = orc_value_channel(in, W, H, pitch, elem_bytes, M, V);
   if (st != ORC_OK) { free(V); return st; }
   memset(S, 0, sizeof(uint64_t) * (size_t)K);
   memset(G, 0, sizeof(uint64_t) * (size_t)K);
   for (int y = 0; y < H; ++y)
     for (int x = 0; x < W; ++x) {
-      S[V[(size_t)y * W + x]] += 1;
-      G[gradient_level(V, W, H, x, y, K, forward)] += 1;
+      S[V[(size_t)y * W + x] >> sh] += 1;
+      G[gradient_level(V, W, H, x, y, M, forward) >> sh] += 1;
     }
   free(V);
   return ORC_OK;
 }
 
+int orc_histograms_v(const void* in, int W, int H, size_t pitch, int elem_bytes, int K, int forward, uint64_t* S,
+                     uint64_t* G) {
+  return orc_histograms_b(in, W, H, pitch, elem_bytes, K, K, forward, S, G);
+}
+
 int orc_histograms(const void* in, int W, int H, size_t pitch, int elem_bytes, int K, uint64_t* S, uint64_t* G) {
   return orc_histograms_v(in, W, H, pitch, elem_bytes, K, 0, S, G);
+}
+
+/* Location of bin k (H_B, Sec. III.A) when K bins cover M data levels: the bin's centre value
+ * normalised to [0, 1], (k w + (w - 1) / 2) / (M - 1) with w = M / K; for M = K this is k / (K - 1). */
+double orc_bin_location(int k, int K, int M) {
+  const int64_t w = M / K;
+  return (double)(2 * (int64_t)k * w + w - 1) / (2.0 * (double)(M - 1));
+}
+
+/* The first k minimising |p - location(k)|: the locations ascend, so the minimum lies next to the
+ * first location >= p; the few neighbours around it are compared in ascending order. */
+static uint32_t nearest_bin(double p, int K, int M) {
+  int lo = 0, hi = K;
+  while (lo < hi) {
+    const int mid = (lo + hi) / 2;
+    if (orc_bin_location(mid, K, M) >= p) hi = mid; else lo = mid + 1;
+  }
+  const int a = lo - 2 < 0 ? 0 : lo - 2, b = lo + 1 > K - 1 ? K - 1 : lo + 1;
+  int best = a;
+  double bd = fabs(p - orc_bin_location(a, K, M));
+  for (int k = a + 1; k <= b; ++k) {
+    const double d = fabs(p - orc_bin_location(k, K, M));
+    if (d < bd) { bd = d; best = k; }
+  }
+  return (uint32_t)best;
+}
+
+/* Class map of binned data: index(i,j) = argmin_k |H_B(R)_i H_B(L)_j - H_B(S)_k| (definition under
+ * Eq. 10) with the bin locations above, first minimum; cmap[i * K + j]. */
+int orc_class_table(int K, int M, uint32_t* cmap) {
+  if (bin_shift(K, M) < 0 || !cmap) return ORC_ERR_INVALID_ARG;
+  for (int i = 0; i < K; ++i) {
+    const double li = orc_bin_location(i, K, M);
+    for (int j = 0; j < K; ++j) cmap[(size_t)i * K + j] = nearest_bin(li * orc_bin_location(j, K, M), K, M);
+  }
+  return ORC_OK;
 }
 
 /* ---------- Stage 3: class map and the two-level optimisation ---------- */
@@ -179,9 +236,14 @@ uint32_t orc_class_index(int K, int i, int j) {
  *      Rn, Ln (Eq. 15 and Eq. 14 results).
  * Any output pointer except Rn, Ln may be NULL.  printed != 0 takes Eq. 13 and Eq. 12 as printed
  * (ORC_VAR_PRINTED_UPDATE): the weight K_ij divides the data term instead of multiplying it. */
-int orc_iterate_v(const uint64_t* S, const uint64_t* G, int K, double alpha, double beta, int printed,
-                  const double* R, const double* L, double* P_out, double* q_out,
-                  double* Ru_out, double* Lu_out, double* Rn, double* Ln) {
+/* The class of cell (i, j): the closed form, or the table of binned data. */
+static uint32_t cell_class(const uint32_t* cmap, int K, int i, int j) {
+  return cmap ? cmap[(size_t)i * K + j] : orc_class_index(K, i, j);
+}
+
+static int iterate_impl(const uint64_t* S, const uint64_t* G, int K, double alpha, double beta, int printed,
+                        const uint32_t* cmap, const double* R, const double* L, double* P_out, double* q_out,
+                        double* Ru_out, double* Lu_out, double* Rn, double* Ln) {
   if (K < 2 || !S || !G || !R || !L || !Rn || !Ln) return ORC_ERR_INVALID_ARG;
   uint64_t Nu = 0;
   for (int k = 0; k < K; ++k) Nu += S[k];
@@ -200,7 +262,7 @@ int orc_iterate_v(const uint64_t* S, const uint64_t* G, int K, double alpha, dou
     if (R[i] == 0.0) continue;
     for (int j = 0; j < K; ++j) {
       if (L[j] == 0.0) continue;
-      uint32_t k = orc_class_index(K, i, j);
+      uint32_t k = cell_class(cmap, K, i, j);
       P[k] = fma(R[i], L[j], P[k]);
     }
   }
@@ -221,7 +283,7 @@ int orc_iterate_v(const uint64_t* S, const uint64_t* G, int K, double alpha, dou
     for (int i = 0; i < K; ++i) {
       double A = 0.0;
       for (int j = 0; j < K; ++j) {
-        const uint32_t k = orc_class_index(K, i, j);
+        const uint32_t k = cell_class(cmap, K, i, j);
         const double Kij = P[k] > 0.0 ? ((R[i] * L[j]) / N) / (P[k] / N) : 0.0;
         if (Kij == 0.0) continue;
         A += (L[j] * (double)S[k]) / (N * Kij);
@@ -234,7 +296,7 @@ int orc_iterate_v(const uint64_t* S, const uint64_t* G, int K, double alpha, dou
     for (int j = 0; j < K; ++j) {
       double B = 0.0;
       for (int i = 0; i < K; ++i) {
-        const uint32_t k = orc_class_index(K, i, j);
+        const uint32_t k = cell_class(cmap, K, i, j);
         const double Kij = P[k] > 0.0 ? ((R[i] * L[j]) / N) / (P[k] / N) : 0.0;
         if (Kij == 0.0) continue;
         B += (Ru[i] * (double)S[k]) / (N * Kij);
@@ -245,7 +307,7 @@ int orc_iterate_v(const uint64_t* S, const uint64_t* G, int K, double alpha, dou
   for (int i = 0; i < K && !printed; ++i) {
     double A = 0.0;
     for (int j = 0; j < K; ++j) {
-      double qk = q[orc_class_index(K, i, j)];
+      double qk = q[cell_class(cmap, K, i, j)];
       if (L2[j] == 0.0 || qk == 0.0) continue;
       A = fma(L2[j], qk, A);
     }
@@ -260,7 +322,7 @@ int orc_iterate_v(const uint64_t* S, const uint64_t* G, int K, double alpha, dou
   for (int j = 0; j < K && !printed; ++j) {
     double B = 0.0;
     for (int i = 0; i < K; ++i) {
-      double qk = q[orc_class_index(K, i, j)];
+      double qk = q[cell_class(cmap, K, i, j)];
       if (RR[i] == 0.0 || qk == 0.0) continue;
       B = fma(RR[i], qk, B);
     }
@@ -282,6 +344,28 @@ int orc_iterate_v(const uint64_t* S, const uint64_t* G, int K, double alpha, dou
   return ORC_OK;
 }
 
+int orc_iterate_v(const uint64_t* S, const uint64_t* G, int K, double alpha, double beta, int printed,
+                  const double* R, const double* L, double* P_out, double* q_out,
+                  double* Ru_out, double* Lu_out, double* Rn, double* Ln) {
+  return iterate_impl(S, G, K, alpha, beta, printed, NULL, R, L, P_out, q_out, Ru_out, Lu_out, Rn, Ln);
+}
+
+/* One iteration on binned data (M levels, K bins): the class map is the table of orc_class_table. */
+int orc_iterate_b(const uint64_t* S, const uint64_t* G, int K, int M, double alpha, double beta, int printed,
+                  const double* R, const double* L, double* P_out, double* q_out,
+                  double* Ru_out, double* Lu_out, double* Rn, double* Ln) {
+  if (bin_shift(K, M) < 0) return ORC_ERR_INVALID_ARG;
+  uint32_t* cmap = NULL;
+  if (M != K) {
+    cmap = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)K * (size_t)K);
+    if (!cmap) return ORC_ERR_INVALID_ARG;
+    orc_class_table(K, M, cmap);
+  }
+  const int st = iterate_impl(S, G, K, alpha, beta, printed, cmap, R, L, P_out, q_out, Ru_out, Lu_out, Rn, Ln);
+  free(cmap);
+  return st;
+}
+
 int orc_iterate(const uint64_t* S, const uint64_t* G, int K, double alpha, double beta,
                 const double* R, const double* L, double* P_out, double* q_out,
                 double* Ru_out, double* Lu_out, double* Rn, double* Ln) {
@@ -299,11 +383,20 @@ int orc_solve(const uint64_t* S, const uint64_t* G, const orc_params* p, double*
   double* Rn = (double*)malloc(sizeof(double) * (size_t)K);
   double* Ln = (double*)malloc(sizeof(double) * (size_t)K);
   if (!Rn || !Ln) { free(Rn); free(Ln); return ORC_ERR_INVALID_ARG; }
+  /* binned data (p->levels = M > K): the class map of the bin locations, built once */
+  const int M = p->levels > 0 ? p->levels : K;
+  uint32_t* cmap = NULL;
+  if (bin_shift(K, M) < 0) { free(Rn); free(Ln); return ORC_ERR_INVALID_ARG; }
+  if (M != K) {
+    cmap = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)K * (size_t)K);
+    if (!cmap) { free(Rn); free(Ln); return ORC_ERR_INVALID_ARG; }
+    orc_class_table(K, M, cmap);
+  }
   for (int k = 0; k < K; ++k) { R[k] = (double)G[k]; L[k] = (double)S[k]; }
   int t = 0;
   while (t < p->max_iter) {
-    orc_iterate_v(S, G, K, p->alpha, p->beta, (p->variants & ORC_VAR_PRINTED_UPDATE) != 0, R, L, NULL, NULL, NULL,
-                  NULL, Rn, Ln);
+    iterate_impl(S, G, K, p->alpha, p->beta, (p->variants & ORC_VAR_PRINTED_UPDATE) != 0, cmap, R, L, NULL, NULL,
+                 NULL, NULL, Rn, Ln);
     double dr = 0.0, dl = 0.0;
     for (int i = 0; i < K; ++i) { double d = Rn[i] - R[i]; dr = fma(d, d, dr); }
     for (int j = 0; j < K; ++j) { double d = Ln[j] - L[j]; dl = fma(d, d, dl); }
@@ -313,7 +406,7 @@ int orc_solve(const uint64_t* S, const uint64_t* G, const orc_params* p, double*
     if (!p->fixed_iters && dr <= p->eps && dl <= p->eps) break;
   }
   if (iters) *iters = t;
-  free(Rn); free(Ln);
+  free(Rn); free(Ln); free(cmap);
   return ORC_OK;
 }
 
@@ -353,13 +446,28 @@ int orc_index1_table(int K, double gamma, uint32_t* idx1) {
   return ORC_OK;
 }
 
+/* index_1 of binned data (M levels, K bins): the same argmin over the bin locations,
+ * idx1[i * K + j] = first k minimising |location(j)^(1/gamma) location(i) - location(k)|. */
+int orc_index1_table_b(int K, int M, double gamma, uint32_t* idx1) {
+  if (bin_shift(K, M) < 0 || !(gamma > 0.0) || !idx1) return ORC_ERR_INVALID_ARG;
+  const double inv_g = 1.0 / gamma;
+  for (int i = 0; i < K; ++i) {
+    const double hr = orc_bin_location(i, K, M);                  /* H_B(R)_i */
+    for (int j = 0; j < K; ++j) {
+      const double hl = pow(orc_bin_location(j, K, M), inv_g);    /* Hbar_B(L)_j, Eq. 17 */
+      idx1[(size_t)i * K + j] = nearest_bin(hl * hr, K, M);       /* Eq. 18-19 */
+    }
+  }
+  return ORC_OK;
+}
+
 /* Eq. 20: H_C(S~)_k = sum over the cells with index_1 = k of the count matrix
  * H_C(R,L)_ij = R_i L_j / N (row-major sums, divided by N at the end). */
-int orc_target(const double* R, const double* L, int K, double gamma, uint64_t N, double* T) {
-  if (K < 2 || !R || !L || !T || N == 0) return ORC_ERR_INVALID_ARG;
+int orc_target_b(const double* R, const double* L, int K, int M, double gamma, uint64_t N, double* T) {
+  if (K < 2 || !R || !L || !T || N == 0 || bin_shift(K, M) < 0) return ORC_ERR_INVALID_ARG;
   uint32_t* idx1 = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)K * (size_t)K);
   if (!idx1) return ORC_ERR_INVALID_ARG;
-  int st = orc_index1_table(K, gamma, idx1);
+  int st = M == K ? orc_index1_table(K, gamma, idx1) : orc_index1_table_b(K, M, gamma, idx1);
   if (st != ORC_OK) { free(idx1); return st; }
   memset(T, 0, sizeof(double) * (size_t)K);
   for (int i = 0; i < K; ++i) {
@@ -375,6 +483,10 @@ int orc_target(const double* R, const double* L, int K, double gamma, uint64_t N
   for (int k = 0; k < K; ++k) T[k] = T[k] / Nd;
   free(idx1);
   return ORC_OK;
+}
+
+int orc_target(const double* R, const double* L, int K, double gamma, uint64_t N, double* T) {
+  return orc_target_b(R, L, K, K, gamma, N, T);
 }
 
 /* ---------- Stage 5: histogram matching (Sec. III.C, last paragraph) ---------- */
@@ -426,9 +538,13 @@ int orc_lut(const uint64_t* S, const double* T, int K, uint16_t* lut) { return o
 
 /* V' = LUT[V]; each channel c becomes round_half_up(c * V' / V) = floor((2 c V' + V) / (2 V)),
  * which keeps the HSV hue and saturation of the pixel; a black pixel (V = 0) becomes grey V'. */
-int orc_apply(const void* in, void* out, int W, int H, size_t in_pitch, size_t out_pitch, int elem_bytes, int K,
-              const uint16_t* lut) {
-  if (!in || !out || !lut || W < 1 || H < 1 || (elem_bytes != 1 && elem_bytes != 2)) return ORC_ERR_INVALID_ARG;
+/* Binned data (M levels, K bins): the LUT maps bins, and the new value keeps the pixel's place in
+ * its bin, V' = LUT[s] w + (V - s w) with s = V >> log2(w), w = M / K. */
+int orc_apply_b(const void* in, void* out, int W, int H, size_t in_pitch, size_t out_pitch, int elem_bytes, int K,
+                int M, const uint16_t* lut) {
+  const int sh = bin_shift(K, M);
+  if (!in || !out || !lut || W < 1 || H < 1 || (elem_bytes != 1 && elem_bytes != 2) || sh < 0)
+    return ORC_ERR_INVALID_ARG;
   int bad = 0;
   for (int y = 0; y < H; ++y) {
     for (int x = 0; x < W; ++x) {
@@ -437,8 +553,9 @@ int orc_apply(const void* in, void* out, int W, int H, size_t in_pitch, size_t o
       for (int ch = 0; ch < 3; ++ch) c[ch] = px(ib, in_pitch, elem_bytes, x, y, ch);
       unsigned V = c[0] > c[1] ? c[0] : c[1];
       V = V > c[2] ? V : c[2];
-      if (V >= (unsigned)K) { bad = 1; V = (unsigned)K - 1; }
-      uint64_t Vp = lut[V];
+      if (V >= (unsigned)M) { bad = 1; V = (unsigned)M - 1; }
+      const unsigned sbin = V >> sh;
+      uint64_t Vp = ((uint64_t)lut[sbin] << sh) | (uint64_t)(V - (sbin << sh));
       unsigned o[3];
       for (int ch = 0; ch < 3; ++ch)
         o[ch] = V == 0 ? (unsigned)Vp : (unsigned)((2ull * c[ch] * Vp + V) / (2ull * V));
@@ -452,20 +569,25 @@ int orc_apply(const void* in, void* out, int W, int H, size_t in_pitch, size_t o
   return bad ? ORC_ERR_RANGE : ORC_OK;
 }
 
+int orc_apply(const void* in, void* out, int W, int H, size_t in_pitch, size_t out_pitch, int elem_bytes, int K,
+              const uint16_t* lut) {
+  return orc_apply_b(in, out, W, H, in_pitch, out_pitch, elem_bytes, K, K, lut);
+}
+
 /* ---------- Whole pipeline ---------- */
 
 int orc_enhance(const void* in, void* out, int W, int H, size_t in_pitch, size_t out_pitch, int elem_bytes,
                 const orc_params* p, uint64_t* S, uint64_t* G, double* R, double* L, double* T,
                 uint16_t* lut, int* iters) {
   if (!p) return ORC_ERR_INVALID_ARG;
-  const int K = p->K;
-  int st = orc_histograms_v(in, W, H, in_pitch, elem_bytes, K, (p->variants & ORC_VAR_FORWARD_GRADIENT) != 0, S, G);
+  const int K = p->K, M = p->levels > 0 ? p->levels : p->K;
+  int st = orc_histograms_b(in, W, H, in_pitch, elem_bytes, K, M, (p->variants & ORC_VAR_FORWARD_GRADIENT) != 0, S, G);
   if (st != ORC_OK) return st;
   st = orc_solve(S, G, p, R, L, iters);
   if (st != ORC_OK) return st;
-  st = orc_target(R, L, K, p->gamma, (uint64_t)W * (uint64_t)H, T);
+  st = orc_target_b(R, L, K, M, p->gamma, (uint64_t)W * (uint64_t)H, T);
   if (st != ORC_OK) return st;
   st = orc_lut_v(S, T, K, (p->variants & ORC_VAR_NEAREST_MATCH) != 0, lut);
   if (st != ORC_OK) return st;
-  return orc_apply(in, out, W, H, in_pitch, out_pitch, elem_bytes, K, lut);
+  return orc_apply_b(in, out, W, H, in_pitch, out_pitch, elem_bytes, K, M, lut);
 }

@@ -54,22 +54,8 @@ def _voronoi_labels(rng: np.random.Generator, W: int, H: int, n_cells: int) -> n
     return labels
 
 
-def low_light_image(
-    W: int,
-    H: int,
-    seed: int,
-    bits: int = 8,
-    n_cells: int = 64,
-    n_blobs: int = 6,
-    illum_lo: float = 0.03,
-    illum_hi: float = 0.35,
-    noise_sigma: float = 2.0 / 255.0,
-) -> np.ndarray:
-    """One synthetic low-light image, shape (H, W, 3), uint8 (bits <= 8) or uint16."""
-    if W < 1 or H < 1:
-        raise ValueError("image must be at least 1x1")
-    rng = np.random.default_rng(seed)
-    M = float((1 << bits) - 1)
+def _scene(rng: np.random.Generator, W: int, H: int, n_cells: int, n_blobs: int):
+    """Reflectance (H, W, 3) and the illumination's shape in [0, 1] (H, W) of one scene."""
     labels = _voronoi_labels(rng, W, H, n_cells)
     colours = rng.uniform(0.2, 1.0, size=(n_cells, 3)).astype(np.float32)
     refl = colours[labels]
@@ -91,11 +77,56 @@ def low_light_image(
         illum = (illum - lo) / (hi - lo)
     else:
         illum[:] = 0.5
+    return refl, illum
+
+
+def low_light_image(
+    W: int,
+    H: int,
+    seed: int,
+    bits: int = 8,
+    n_cells: int = 64,
+    n_blobs: int = 6,
+    illum_lo: float = 0.03,
+    illum_hi: float = 0.35,
+    noise_sigma: float = 2.0 / 255.0,
+) -> np.ndarray:
+    """One synthetic low-light image, shape (H, W, 3), uint8 (bits <= 8) or uint16."""
+    if W < 1 or H < 1:
+        raise ValueError("image must be at least 1x1")
+    rng = np.random.default_rng(seed)
+    M = float((1 << bits) - 1)
+    refl, illum = _scene(rng, W, H, n_cells, n_blobs)
     illum = illum_lo + (illum_hi - illum_lo) * illum
 
     img = refl * illum[:, :, None]
     img += rng.standard_normal((H, W, 3), dtype=np.float32) * np.float32(noise_sigma)
     np.clip(img, 0.0, 1.0, out=img)
+    img = np.floor(img * np.float32(M) + np.float32(0.5))
+    return img.astype(np.uint8 if bits <= 8 else np.uint16)
+
+
+def normal_light_image(
+    W: int,
+    H: int,
+    seed: int,
+    bits: int = 8,
+    n_cells: int = 64,
+    n_blobs: int = 6,
+    illum_lo: float = 0.45,
+    illum_hi: float = 0.95,
+) -> np.ndarray:
+    """The scene of low_light_image(W, H, seed, ...) under normal light: the same reflectance and
+    illumination shape with the illumination rescaled into [illum_lo, illum_hi], without noise (a
+    reference image the generator knows, standing in for the paired normal-light images of the
+    paper's datasets)."""
+    if W < 1 or H < 1:
+        raise ValueError("image must be at least 1x1")
+    rng = np.random.default_rng(seed)
+    M = float((1 << bits) - 1)
+    refl, illum = _scene(rng, W, H, n_cells, n_blobs)
+    illum = illum_lo + (illum_hi - illum_lo) * illum
+    img = np.clip(refl * illum[:, :, None], 0.0, 1.0)
     img = np.floor(img * np.float32(M) + np.float32(0.5))
     return img.astype(np.uint8 if bits <= 8 else np.uint16)
 

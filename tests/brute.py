@@ -222,3 +222,54 @@ def lut_nearest(S, T):
         d = [abs(CT[z] * N - int(CS[s]) * TT) for z in range(K)]
         out[s] = d.index(min(d))
     return out
+
+
+# ---- binned data: K bins over M data levels ----
+
+def bin_locations_exact(K, M):
+    """Bin centre values normalised to [0, 1], as exact rationals: (k w + (w - 1)/2) / (M - 1)."""
+    w = M // K
+    return [Fraction(2 * k * w + w - 1, 2 * (M - 1)) for k in range(K)]
+
+
+def nearest_exact(p, locs):
+    """(first k minimising |p - loc_k|, whether the minimum is shared by two levels), exactly."""
+    d = [abs(p - x) for x in locs]
+    m = min(d)
+    ks = [k for k, v in enumerate(d) if v == m]
+    return ks[0], len(ks) > 1
+
+
+def class_map_binned_float(K, M, gamma=None):
+    """Class map (gamma None) or index_1 map over the bin locations by a literal FP64 argmin."""
+    w = M // K
+    loc = np.array([(2 * k * w + w - 1) / (2.0 * (M - 1)) for k in range(K)])
+    lj = loc if gamma is None else np.array([math.pow(x, 1.0 / gamma) for x in loc])
+    hlm = np.outer(loc, lj)
+    return np.argmin(np.abs(hlm[:, :, None] - loc[None, None, :]), axis=2)
+
+
+def histograms_binned(img, K, M):
+    V = value_channel(img)
+    sh = int(round(math.log2(M // K)))
+    S = np.bincount((V >> sh).ravel(), minlength=K).astype(np.int64)
+    G = np.bincount((sobel_levels(V, M) >> sh).ravel(), minlength=K).astype(np.int64)
+    return S, G
+
+
+def apply_binned(img, lut_, K, M):
+    """V' = LUT[s] w + (V - s w) (s = V >> log2 w); channels c -> nearest integer to c V'/V, halves up."""
+    sh = int(round(math.log2(M // K)))
+    H, W, _ = img.shape
+    out = np.zeros_like(img)
+    for y in range(H):
+        for x in range(W):
+            c = [int(v) for v in img[y, x]]
+            V = max(c)
+            s = V >> sh
+            Vp = (int(lut_[s]) << sh) + (V - (s << sh))
+            if V == 0:
+                out[y, x] = (Vp, Vp, Vp)
+            else:
+                out[y, x] = [math.floor(Fraction(ch * Vp, V) + Fraction(1, 2)) for ch in c]
+    return out
