@@ -85,7 +85,16 @@ enum {
 /* Method parameters.  alpha, beta: weights of the illumination and reflectance priors
  * (Eq. 9); gamma: Eq. 17; eps, max_iter: stopping threshold and iteration cap T of
  * Algorithm 1 (stop when both squared changes are <= eps, or after max_iter).
- * K must be a power of two in [8, 4096]; elem_bytes = 1 needs K <= 256. */
+ * K must be a power of two in [8, 4096]; elem_bytes = 1 needs K <= 256.
+ * levels: 0 (one bin per level: the data's levels are 0 .. K-1), or M, a power of two in
+ * [K, 4096], the data's levels binned into the K bins ("l levels", Sec. II preamble, with fewer
+ * bins than levels, e.g. K = 256 on 12-bit data, M = 4096): value v falls into bin
+ * v >> log2(M / K); bin k is located at its centre value, (k w + (w - 1)/2) / (M - 1) with
+ * w = M / K (the location histogram of Sec. III.A; for M = K this is k / (K - 1)); the class maps
+ * of Eq. 10 and Eq. 19 are the argmins over those locations; the gradient level is clipped to M - 1
+ * and binned likewise; the LUT maps bins, and a pixel's new value keeps its place in its bin,
+ * V' = LUT[s] w + (V - s w).  Values >= M are a range error.  8-bit data needs M <= 256.  The
+ * binned form runs the generic pixel kernels. */
 typedef struct {
   int K;
   double alpha;
@@ -95,6 +104,7 @@ typedef struct {
   int max_iter;
   int precision;   /* hr_precision */
   unsigned flags;  /* HR_FLAG_* */
+  int levels;      /* 0, or M: data levels binned into the K bins */
 } hr_params;
 
 typedef struct hr_ctx hr_ctx;
@@ -134,7 +144,7 @@ typedef struct {
 } hr_tuning;
 
 /* Fills *p with the defaults: K = 256, alpha = beta = 1e-3, gamma = 2.2 (Sec. III.C),
- * eps = 0, max_iter = 10 (Sec. IV.C), FP64, fixed iterations. */
+ * eps = 0, max_iter = 10 (Sec. IV.C), FP64, fixed iterations, levels = 0. */
 void histretinex_default_params(hr_params* p);
 
 /* Creates a context on `device` for parameters *p (copied).  Builds the per-K tables
@@ -196,7 +206,7 @@ hr_status histretinex_enhance_host_many(hr_ctx* ctx, int n, const void* const* h
  * histretinex_enhance) for K <= 256, with its whole workspace in one 1 MiB array that the library
  * declares in device memory; that array stays resident on every device that loads the library
  * until the process exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
- * K > 256 returns HR_ERR_UNSUPPORTED.  Each call looks up the array's address on the current
+ * K > 256 and binned data (levels other than 0 or K) return HR_ERR_UNSUPPORTED.  Each call looks up the array's address on the current
  * device (cudaGetSymbolAddress, which allocates nothing; the first call on a device may load the
  * library's device code, so make it before any stream capture), then queues on `stream` two
  * memsets (the histograms it accumulates and its status word) and four kernels (its own table of

@@ -40,6 +40,7 @@ class hr_params(ctypes.Structure):
         ("max_iter", ctypes.c_int),
         ("precision", ctypes.c_int),
         ("flags", ctypes.c_uint),
+        ("levels", ctypes.c_int),
     ]
 
 
@@ -138,12 +139,14 @@ class Params:
     printed_update: bool = False    # Eq. 12 / Eq. 13 as printed (the weight K_ij divides)
     nearest_match: bool = False     # matching to the nearest cumulative share
     forward_gradient: bool = False  # gradient image by forward differences
+    levels: int = 0                 # M data levels binned into the K bins (0: M = K)
 
     def c(self) -> hr_params:
         flags = (FLAG_FIXED_ITERS if self.fixed_iters else 0) | (FLAG_DEBUG_OUT if self.debug else 0) | \
             (FLAG_STAGE_TIMING if self.stage_timing else 0) | (FLAG_PRINTED_UPDATE if self.printed_update else 0) | \
             (FLAG_NEAREST_MATCH if self.nearest_match else 0) | (FLAG_FORWARD_GRADIENT if self.forward_gradient else 0)
-        return hr_params(self.K, self.alpha, self.beta, self.gamma, self.eps, self.max_iter, self.precision, flags)
+        return hr_params(self.K, self.alpha, self.beta, self.gamma, self.eps, self.max_iter, self.precision, flags,
+                         self.levels)
 
 
 def _check(code, what=""):

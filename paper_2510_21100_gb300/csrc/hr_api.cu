@@ -21,6 +21,9 @@ struct hr_ctx {
   uint8_t* d_slots = nullptr;
   int n_slots = 0;
   uint16_t* d_jstart1 = nullptr;   // [K][K+1], index_1 class boundaries (Eq. 19)
+  uint16_t* d_cmap = nullptr;      // binned data: class map of Eq. 10 [K][K] and its boundaries [K][K+1]
+  uint16_t* d_jstart0 = nullptr;
+  int M = 0;                       // the data's levels (K unless binned)
   unsigned* d_status = nullptr;
   ImageDesc* d_imgs = nullptr;
   int* d_tile_start = nullptr;
@@ -84,7 +87,47 @@ hr_status check_params(const hr_params* p) {
   // the printed update's values (S_k P_k, up to about N^3 / K, and reflectance bins that shrink
   // towards zero) leave FP32's exponent range, which the FP32 and double-float forms share
   if ((p->flags & HR_FLAG_PRINTED_UPDATE) && p->precision != HR_PREC_FP64) return HR_ERR_UNSUPPORTED;
+  if (p->levels != 0 && (!pow2(p->levels) || p->levels < p->K || p->levels > 4096)) return HR_ERR_INVALID_ARG;
   return HR_OK;
+}
+
+// Location of bin k of K bins over M data levels: the bin's centre value normalised to [0, 1],
+// (k w + (w - 1) / 2) / (M - 1), w = M / K (for M = K: k / (K - 1)).
+static double bin_location(int k, int K, int M) {
+  const long long w = M / K;
+  return (double)(2 * (long long)k * w + w - 1) / (2.0 * (double)(M - 1));
+}
+
+// The first bin whose location is nearest to p (locations ascend: the minimum lies next to the
+// first location >= p).
+static int nearest_bin(double p, int K, int M) {
+  int lo = 0, hi = K;
+  while (lo < hi) {
+    const int mid = (lo + hi) / 2;
+    if (bin_location(mid, K, M) >= p) hi = mid; else lo = mid + 1;
+  }
+  const int a = lo - 2 < 0 ? 0 : lo - 2, b = lo + 1 > K - 1 ? K - 1 : lo + 1;
+  int best = a;
+  double bd = std::fabs(p - bin_location(a, K, M));
+  for (int k = a + 1; k <= b; ++k) {
+    const double d = std::fabs(p - bin_location(k, K, M));
+    if (d < bd) { bd = d; best = k; }
+  }
+  return best;
+}
+
+void build_class_tables(int K, int M, uint16_t* cmap, uint16_t* js0) {
+  for (int i = 0; i < K; ++i) {
+    const double li = bin_location(i, K, M);
+    uint16_t* row = js0 + (size_t)i * (K + 1);
+    int k = 0;
+    for (int j = 0; j < K; ++j) {
+      const int c = nearest_bin(li * bin_location(j, K, M), K, M);
+      cmap[(size_t)i * K + j] = (uint16_t)c;
+      while (k <= c) row[k++] = (uint16_t)j;
+    }
+    while (k <= K) row[k++] = (uint16_t)K;
+  }
 }
 
 // index_1(i, j) (Eq. 17-19): the level whose location k/(K-1) is nearest to the gamma-processed
@@ -105,16 +148,17 @@ static int index1(int K, double hl, double hr) {
 }
 
 // jstart1[i][k] = first illumination bin j with index_1(i, j) >= k (index_1 grows with j).
-void build_jstart1(int K, double gamma, uint16_t* t) {
+void build_jstart1(int K, double gamma, uint16_t* t, int M) {
+  const bool binned = M > K;
   const double km1 = (double)(K - 1);
   const double ig = 1.0 / gamma;
-  auto hl = [&](int j) { return std::pow((double)j / km1, ig); };
+  auto hl = [&](int j) { return std::pow(binned ? bin_location(j, K, M) : (double)j / km1, ig); };
   for (int i = 0; i < K; ++i) {
-    const double hr = (double)i / km1;
+    const double hr = binned ? bin_location(i, K, M) : (double)i / km1;
     uint16_t* row = t + (size_t)i * (K + 1);
     int k = 0;
     for (int j = 0; j < K; ++j) {
-      const int c = index1(K, hl(j), hr);
+      const int c = binned ? nearest_bin(hl(j) * hr, K, M) : index1(K, hl(j), hr);
       while (k <= c) row[k++] = (uint16_t)j;
     }
     while (k <= K) row[k++] = (uint16_t)K;
@@ -255,6 +299,8 @@ hr::SolveArgs solve_args(const hr_ctx* c, const Group& g) {
   a.zero_hist = debug ? 0 : 1;
   a.printed = (c->p.flags & HR_FLAG_PRINTED_UPDATE) ? 1 : 0;
   a.nearest = (c->p.flags & HR_FLAG_NEAREST_MATCH) ? 1 : 0;
+  a.cmap = c->d_cmap;
+  a.jstart0 = c->d_jstart0;
   a.arith = c->p.precision == HR_PREC_FP32 ? hr::kArithF32 : (c->p.precision == HR_PREC_DF64 ? hr::kArithDF64 : hr::kArithF64);
   return a;
 }
@@ -291,7 +337,7 @@ cudaError_t enqueue_stages(hr_ctx* c, const Group& g, int elem_bytes, bool fast_
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
   e = hr::launch_hist(g.tab, g.total, g.units, g.interior, elem_bytes, K, g.slots, c->lay.bytes, c->lay, c->d_status,
                       c->sm_count, c->tune.hist_ctas_per_sm, st, fast_in, (pdl & 1) != 0,
-                      (c->p.flags & HR_FLAG_FORWARD_GRADIENT) != 0);
+                      (c->p.flags & HR_FLAG_FORWARD_GRADIENT) != 0, c->M);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
   if (after_hist && (e = cudaEventRecord(after_hist, st)) != cudaSuccess) return e;
@@ -301,7 +347,7 @@ cudaError_t enqueue_stages(hr_ctx* c, const Group& g, int elem_bytes, bool fast_
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
   e = hr::launch_apply(g.tab, g.total, elem_bytes, K, g.slots, c->lay.bytes, c->lay, c->d_status, c->sm_count,
-                       c->tune.apply_ctas_per_sm, st, fast_out, (pdl & 4) != 0);
+                       c->tune.apply_ctas_per_sm, st, fast_out, (pdl & 4) != 0, c->M);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return e;
   return cudaSuccess;
@@ -411,12 +457,12 @@ hr_status run_partitioned(hr_ctx* c, const ImageDesc& d, int elem_bytes, bool fa
       if (e != cudaSuccess) return e;
     }
     return hr::launch_hist(g.tab, g.total, g.units, g.interior, elem_bytes, K, g.slots, c->lay.bytes, c->lay,
-                           c->d_status, sms, c->tune.hist_ctas_per_sm, s, fast_in, false, forward);
+                           c->d_status, sms, c->tune.hist_ctas_per_sm, s, fast_in, false, forward, c->M);
   };
   auto solve = [&](cudaStream_t s) { return hr::launch_solve(a, 1, solve_ctas(c, 1, false), s, false); };
   auto apply = [&](cudaStream_t s) {
     return hr::launch_apply(g.tab, g.total, elem_bytes, K, g.slots, c->lay.bytes, c->lay, c->d_status, sms,
-                            c->tune.apply_ctas_per_sm, s, fast_out, false);
+                            c->tune.apply_ctas_per_sm, s, fast_out, false, c->M);
   };
   const cudaError_t e = hr::partitions_run(c->part, r, st, hist, solve, apply);
   c->ring_clean[r] = e == cudaSuccess && !debug;
@@ -433,7 +479,7 @@ hr_status run_partitioned(hr_ctx* c, const ImageDesc& d, int elem_bytes, bool fa
 hr_status run_pipeline(hr_ctx* c, int n, const ImageDesc* imgs, int elem_bytes, cudaStream_t st, bool batched) {
   const int K = c->p.K;
   if (elem_bytes != 1 && elem_bytes != 2) return HR_ERR_INVALID_ARG;
-  if (elem_bytes == 1 && K > 256) return HR_ERR_INVALID_ARG;
+  if (elem_bytes == 1 && (K > 256 || c->M > 256)) return HR_ERR_INVALID_ARG;
   long long total = 0, units = 0;
   for (int i = 0; i < n; ++i) {
     const ImageDesc& d = imgs[i];
@@ -636,6 +682,7 @@ void histretinex_default_params(hr_params* p) {
   p->max_iter = 10;
   p->precision = HR_PREC_FP64;
   p->flags = HR_FLAG_FIXED_ITERS;
+  p->levels = 0;
 }
 
 hr_status histretinex_create(hr_ctx** out, const hr_params* p, int device) {
@@ -652,11 +699,20 @@ hr_status histretinex_create(hr_ctx** out, const hr_params* p, int device) {
   c->device = device;
   c->p = *p;
   c->lay = hr::make_layout(p->K);
+  c->M = p->levels > 0 ? p->levels : p->K;
   cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
   std::vector<uint16_t> js((size_t)p->K * (p->K + 1));
-  hr::build_jstart1(p->K, p->gamma, js.data());
+  hr::build_jstart1(p->K, p->gamma, js.data(), c->M);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_jstart1, js.size() * sizeof(uint16_t));
   if (e == cudaSuccess) e = cudaMemcpy(c->d_jstart1, js.data(), js.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && c->M != p->K) {  // binned data: the class map of Eq. 10 as tables
+    std::vector<uint16_t> cm((size_t)p->K * p->K), j0((size_t)p->K * (p->K + 1));
+    hr::build_class_tables(p->K, c->M, cm.data(), j0.data());
+    e = cudaMalloc(&c->d_cmap, cm.size() * sizeof(uint16_t));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_jstart0, j0.size() * sizeof(uint16_t));
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_cmap, cm.data(), cm.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_jstart0, j0.data(), j0.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->desc_done, cudaEventDisableTiming);
@@ -855,6 +911,8 @@ hr_status histretinex_destroy(hr_ctx* c) {
     if (c->ring_free[i]) cudaEventDestroy(c->ring_free[i]);
   cudaFree(c->d_slots);
   cudaFree(c->d_jstart1);
+  cudaFree(c->d_cmap);
+  cudaFree(c->d_jstart0);
   cudaFree(c->d_status);
   cudaFree(c->d_imgs);
   cudaFree(c->d_tile_start);

@@ -94,7 +94,11 @@ SlotLayout make_layout(int K);
 // Parameter validation of hr_params (HR_OK or HR_ERR_INVALID_ARG).
 hr_status check_params(const hr_params* p);
 // Eq. 19 class boundaries: t[i * (K + 1) + k] = first illumination bin j with index_1(i, j) >= k.
-void build_jstart1(int K, double gamma, uint16_t* t);
+// M: the data's levels (K bins of M / K levels each, bins located at their centre values).
+void build_jstart1(int K, double gamma, uint16_t* t, int M = 0);
+// Binned data: the class map of Eq. 10 over the bin locations, cmap[i * K + j], and its boundaries
+// js0[i * (K + 1) + k] = first j with cmap[i][j] >= k.
+void build_class_tables(int K, int M, uint16_t* cmap, uint16_t* js0);
 
 // Number of solver vectors (double[K]) and their shared-memory footprint.
 constexpr int kSolveVecs = 8;       // Rc, Lc, L2c, RRc, Ru, Lu, q, spare
@@ -121,6 +125,8 @@ struct SolveArgs {
   int zero_hist;             // 1: clear H_C(S) and H_C(grad S) after use, ready for the next call
   int printed;               // 1: Eq. 12 / Eq. 13 as printed (the weight K_ij divides)
   int nearest;               // 1: matching to the nearest cumulative share
+  const uint16_t* cmap;      // binned data: class map of Eq. 10 [K][K] (nullptr: the closed form)
+  const uint16_t* jstart0;   // binned data: its boundaries [K][K+1], first j with class >= k
 };
 
 // Launchers (return cudaError_t of the launch).  pdl: programmatic dependent launch (the kernel
@@ -131,14 +137,15 @@ struct SolveArgs {
 // interior strips (strips that cross no right or bottom image edge).  Tile kernels
 // run sms x ctas_per_sm CTAs, the strip kernel one CTA per SM.
 // forward: the gradient image by forward differences (generic kernel) instead of the Sobel operator.
+// M > K: binned data (value v in bin v >> log2(M / K); generic kernel).
 cudaError_t launch_hist(const ImgTab& tab, int total_tiles, int total_units, int interior_units, int elem_bytes,
                         int K, uint8_t* slots,
                         size_t slot_bytes, SlotLayout lay, unsigned* status, int sms, int ctas_per_sm,
-                        cudaStream_t st, bool fast, bool pdl, bool forward = false);
+                        cudaStream_t st, bool fast, bool pdl, bool forward = false, int M = 0);
 cudaError_t launch_solve(const SolveArgs& a, int n, int cluster, cudaStream_t st, bool pdl);
 cudaError_t launch_apply(const ImgTab& tab, int total_tiles, int elem_bytes, int K, uint8_t* slots, size_t slot_bytes,
                          SlotLayout lay, unsigned* status, int sms, int ctas_per_sm, cudaStream_t st, bool fast,
-                         bool pdl);
+                         bool pdl, int M = 0);
 // Gradient levels of squared magnitudes [m2_first, m2_first + n) by one of the histogram kernels'
 // three device forms (0: strip kernel, 1: staged-tile kernel, 2: generic kernel), into out[n].
 cudaError_t launch_grad_level_probe(int form, int K, int m2_first, int n, uint16_t* out, cudaStream_t st);

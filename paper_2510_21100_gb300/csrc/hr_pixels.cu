@@ -48,7 +48,7 @@ __device__ __forceinline__ unsigned round_sqrt(unsigned m2) {
 template <typename ET>
 __global__ void __launch_bounds__(kThreads) hist_kernel(const ImgTab tab, int total, int K,
                                                         uint8_t* slots, size_t slot_bytes, SlotLayout lay,
-                                                        unsigned* status, int forward) {
+                                                        unsigned* status, int forward, int shift, int M) {
   pdl_wait();     // the previous kernel on the stream has finished
   pdl_trigger();  // the next one may be scheduled (it waits for this one)
   const int n = tab.n;
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kThreads) hist_kernel(const ImgTab tab, int to
       const int r = e / kVW, c = e - r * kVW;
       const int y = clampi(y0 - 1 + r, 0, im.H - 1), x = clampi(x0 - 1 + c, 0, im.W - 1);
       unsigned v = load_value<ET>(im, x, y);
-      if (v >= (unsigned)K) { range_bad = true; v = K - 1; }
+      if (v >= (unsigned)M) { range_bad = true; v = M - 1; }  // (M = K unless the data is binned)
       vt[r * kVW + c] = (unsigned short)v;
     }
     __syncthreads();
@@ -111,9 +111,10 @@ __global__ void __launch_bounds__(kThreads) hist_kernel(const ImgTab tab, int to
       const int gx = forward ? a12 - a11 : (a02 + 2 * a12 + a22) - (a00 + 2 * a10 + a20);
       const int gy = forward ? a21 - a11 : (a20 + 2 * a21 + a22) - (a00 + 2 * a01 + a02);
       unsigned g = round_sqrt((unsigned)(gx * gx + gy * gy));
-      g = g < (unsigned)(K - 1) ? g : (unsigned)(K - 1);
-      atomicAdd(my_hs + a11, 1u);
-      atomicAdd(my_hg + g, 1u);
+      g = g < (unsigned)(M - 1) ? g : (unsigned)(M - 1);
+      // binned data: value v and gradient level g (clipped to the data's range) fall into bins >> shift
+      atomicAdd(my_hs + (a11 >> shift), 1u);
+      atomicAdd(my_hg + (g >> shift), 1u);
     }
     __syncthreads();
   }
@@ -134,14 +135,16 @@ __global__ void __launch_bounds__(kThreads) hist_kernel(const ImgTab tab, int to
 template <typename ET>
 __global__ void __launch_bounds__(kThreads) apply_kernel(const ImgTab tab, int total, int K,
                                                          const uint8_t* slots, size_t slot_bytes, SlotLayout lay,
-                                                         unsigned* status) {
+                                                         unsigned* status, int shift, int M) {
   pdl_wait();     // the previous kernel on the stream has finished
   pdl_trigger();  // the next one may be scheduled (it waits for this one)
   const int n = tab.n;
   const int* __restrict__ tile_start = tab.tiles;  // (n > 1 only)
   extern __shared__ __align__(16) unsigned char smem[];
+  // per value V (8-bit data: M <= 256 entries) or per bin (16-bit data: K entries)
+  const int nt = sizeof(ET) == 1 ? M : K;
   unsigned short* lut = reinterpret_cast<unsigned short*>(smem);
-  float* rup = reinterpret_cast<float*>(smem + ((K * 2 + 15) & ~15));  // V'/V rounded up (8-bit data)
+  float* rup = reinterpret_cast<float*>(smem + ((nt * 2 + 15) & ~15));  // V'/V rounded up (8-bit data)
   const int tid = threadIdx.x;
   const int chunk = (total + gridDim.x - 1) / gridDim.x;
   const int t0 = blockIdx.x * chunk, t1 = min(total, t0 + chunk);
@@ -152,8 +155,11 @@ __global__ void __launch_bounds__(kThreads) apply_kernel(const ImgTab tab, int t
     if (img != cur) {
       __syncthreads();
       const unsigned short* gl = reinterpret_cast<const unsigned short*>(slots + (size_t)img * slot_bytes + lay.lut);
-      for (int k = tid; k < K; k += kThreads) {
-        const unsigned short vp = gl[k];
+      for (int k = tid; k < nt; k += kThreads) {
+        // V' of value k: binned data keeps the value's place in its bin, LUT[s] w + (k - s w)
+        const int sb = sizeof(ET) == 1 ? k >> shift : k;
+        const unsigned short vp =
+            sizeof(ET) == 1 ? (unsigned short)(((unsigned)gl[sb] << shift) | (unsigned)(k - (sb << shift))) : gl[k];
         lut[k] = vp;
         if (sizeof(ET) == 1) rup[k] = k > 0 ? __fdiv_ru((float)vp, (float)k) : 0.0f;
       }
@@ -172,8 +178,8 @@ __global__ void __launch_bounds__(kThreads) apply_kernel(const ImgTab tab, int t
       unsigned ch[3] = {src[0], src[1], src[2]};
       unsigned V = ch[0] > ch[1] ? ch[0] : ch[1];
       V = V > ch[2] ? V : ch[2];
-      if (V >= (unsigned)K) { range_bad = true; V = K - 1; }
-      const unsigned vp = lut[V];
+      if (V >= (unsigned)M) { range_bad = true; V = M - 1; }
+      const unsigned vp = sizeof(ET) == 1 ? lut[V] : ((unsigned)lut[V >> shift] << shift) | (V & ((1u << shift) - 1u));
       ET* dst = reinterpret_cast<ET*>(im.out + (long long)y * im.out_pitch) + 3 * x;
       if (V == 0) {
         dst[0] = (ET)vp; dst[1] = (ET)vp; dst[2] = (ET)vp;
@@ -883,9 +889,12 @@ cudaError_t launch_grad_level_probe(int form, int K, int m2_first, int n, uint16
 cudaError_t launch_hist(const ImgTab& tab, int total_tiles, int total_units, int interior_units, int elem_bytes,
                         int K, uint8_t* slots,
                         size_t slot_bytes, SlotLayout lay, unsigned* status, int sms, int ctas_per_sm,
-                        cudaStream_t st, bool fast, bool pdl, bool forward) {
+                        cudaStream_t st, bool fast, bool pdl, bool forward, int M) {
   const int copies = K <= 256 ? kWarps : 1;
-  if (forward) fast = false;  // the forward-difference gradient runs on the generic kernel
+  if (M <= 0) M = K;
+  int shift = 0;
+  while ((K << shift) < M) ++shift;
+  if (forward || M != K) fast = false;  // forward differences and binned data run on the generic kernel
   const size_t smem = (size_t)2 * copies * K * sizeof(unsigned) + (size_t)kVH * kVW * sizeof(unsigned short);
   // strips when the launch has at least HR_STRIP_MIN_FACTOR of them per warp of a full grid (one
   // large image or a large batch), staged tiles otherwise
@@ -913,26 +922,31 @@ cudaError_t launch_hist(const ImgTab& tab, int total_tiles, int total_units, int
   if (elem_bytes == 1) {
     cudaFuncSetAttribute(hist_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return launch_kernel(hist_kernel<uint8_t>, dim3(grid), dim3(kThreads), smem, st, pdl, tab, total_tiles, K, slots,
-                         slot_bytes, lay, status, (int)forward);
+                         slot_bytes, lay, status, (int)forward, shift, M);
   }
   cudaFuncSetAttribute(hist_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return launch_kernel(hist_kernel<uint16_t>, dim3(grid), dim3(kThreads), smem, st, pdl, tab, total_tiles, K, slots,
-                       slot_bytes, lay, status, (int)forward);
+                       slot_bytes, lay, status, (int)forward, shift, M);
 }
 
 cudaError_t launch_apply(const ImgTab& tab, int total_tiles, int elem_bytes, int K, uint8_t* slots, size_t slot_bytes,
                          SlotLayout lay, unsigned* status, int sms, int ctas_per_sm, cudaStream_t st, bool fast,
-                         bool pdl) {
-  const size_t smem = (size_t)((K * 2 + 15) & ~15) + (size_t)K * sizeof(float);
+                         bool pdl, int M) {
+  if (M <= 0) M = K;
+  int shift = 0;
+  while ((K << shift) < M) ++shift;
+  if (M != K) fast = false;  // binned data: the generic kernel
+  const int nt = elem_bytes == 1 ? M : K;
+  const size_t smem = (size_t)((nt * 2 + 15) & ~15) + (size_t)nt * sizeof(float);
   const int grid = max(1, min(sms * ctas_per_sm, total_tiles));
   if (elem_bytes == 1 && fast)
     return launch_kernel(apply_u8v_kernel, dim3(grid), dim3(kThreads), 0, st, pdl, tab, total_tiles, K, slots,
                          slot_bytes, lay, status);
   if (elem_bytes == 1)
     return launch_kernel(apply_kernel<uint8_t>, dim3(grid), dim3(kThreads), smem, st, pdl, tab, total_tiles, K, slots,
-                         slot_bytes, lay, status);
+                         slot_bytes, lay, status, shift, M);
   return launch_kernel(apply_kernel<uint16_t>, dim3(grid), dim3(kThreads), smem, st, pdl, tab, total_tiles, K, slots,
-                       slot_bytes, lay, status);
+                       slot_bytes, lay, status, shift, M);
 }
 
 }  // namespace hr

@@ -158,8 +158,10 @@ struct JsIndex {
   int K;
   const uint16_t* RI;
   const unsigned long long* mg;
+  const uint16_t* js0;  // binned data: the boundary table [K][K+1] of the class map (else nullptr)
   __device__ int operator()(int a, int k) const {
     const int i = RI[a];
+    if (js0) return js0[(size_t)i * (K + 1) + k];
     if (!mg) return jstart_index(i, k, K);
     if (k <= 0) return 0;
     if (i == 0) return K;
@@ -578,7 +580,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     for (int a = tid; a < nR; a += NT) mg[a] = RI[a] ? ~0ull / (2ull * RI[a]) + 1ull : 0ull;
     __syncthreads();
   }
-  const ClassPlan PP = plan_classes(cl, nR, nL, RI, posL, JsIndex{K, RI, mg}, [&](int c) { return (int)LJ[c]; }, csz, cst,
+  const ClassPlan PP = plan_classes(cl, nR, nL, RI, posL, JsIndex{K, RI, mg, A.jstart0}, [&](int c) { return (int)LJ[c]; }, csz, cst,
                                     pst, ob, ured, rank, C);
   stamp();
   // owner CTA of every class of the plan: rank r holds the classes whose first cell lies in
@@ -676,8 +678,13 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         F acc = 0.0;
         if (a < aB) {
           const int i = RI[a];
+          if (A.cmap) {  // binned data: the class map's table
+            const uint16_t* crow = A.cmap + (size_t)i * K;
+            for (int b = gl; b < nL; b += GA) acc = fmaF(L2c[b], q[crow[LJ[b]]], acc);
+          } else {
 #pragma unroll kSumUnroll
-          for (int b = gl; b < nL; b += GA) acc = fmaF(L2c[b], q[class_index(i, LJ[b], km1, cdiv)], acc);
+            for (int b = gl; b < nL; b += GA) acc = fmaF(L2c[b], q[class_index(i, LJ[b], km1, cdiv)], acc);
+          }
         }
         for (int o = GA >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
         if (gl == 0 && a < aB) {
@@ -720,8 +727,12 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         F acc = 0.0;
         if (b < bB) {
           const int j = LJ[b];
+          if (A.cmap) {
+            for (int a = gl; a < nR; a += GB) acc = fmaF(RRc[a], q[A.cmap[(size_t)RI[a] * K + j]], acc);
+          } else {
 #pragma unroll kSumUnroll
-          for (int a = gl; a < nR; a += GB) acc = fmaF(RRc[a], q[class_index(RI[a], j, km1, cdiv)], acc);
+            for (int a = gl; a < nR; a += GB) acc = fmaF(RRc[a], q[class_index(RI[a], j, km1, cdiv)], acc);
+          }
         }
         for (int o = GB >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
         if (gl == 0 && b < bB) Bs[b] = acc;

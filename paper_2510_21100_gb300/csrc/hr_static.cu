@@ -83,6 +83,7 @@ extern "C" hr_status histretinex_enhance_noalloc(const hr_params* p, const void*
   hr_status s = hr::check_params(p);
   if (s != HR_OK) return s;
   if (p->K > kStaticMaxK) return HR_ERR_UNSUPPORTED;  // the static workspace is sized for K <= 256
+  if (p->levels != 0 && p->levels != p->K) return HR_ERR_UNSUPPORTED;  // no binned data here
   if (!d_in || !d_out || width < 1 || height < 1 || (elem_bytes != 1 && elem_bytes != 2)) return HR_ERR_INVALID_ARG;
   const size_t row = (size_t)3 * width * elem_bytes;
   if (in_pitch < row || out_pitch < row) return HR_ERR_INVALID_ARG;

@@ -19,7 +19,7 @@ def params_pair(**kw):
     variants = (oracle.VAR_PRINTED_UPDATE if p.printed_update else 0) | \
         (oracle.VAR_NEAREST_MATCH if p.nearest_match else 0) | (oracle.VAR_FORWARD_GRADIENT if p.forward_gradient else 0)
     po = oracle.Params(K=p.K, alpha=p.alpha, beta=p.beta, gamma=p.gamma, eps=p.eps, max_iter=p.max_iter,
-                       fixed_iters=p.fixed_iters, variants=variants)
+                       fixed_iters=p.fixed_iters, variants=variants, levels=p.levels)
     return p, po
 
 
