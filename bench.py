@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--height", type=int, default=4320)
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, per-size and CPU-baseline legs")
     ap.add_argument("--streams", type=int, default=4, help="CUDA streams the timed steps go to, round-robin")
+    ap.add_argument("--serving-seconds", type=float, default=0.0,
+                    help="long serving runs: seconds per rate (first 5 s left out of the statistics)")
+    ap.add_argument("--serving-rates", default="800,1600", help="request rates of the long serving runs")
     return ap.parse_args()
 
 
@@ -137,6 +140,25 @@ def cpu_oracle_rate(imgs_np, seconds=10.0, rows=None):
     return mp / el, done, img.shape
 
 
+def cpu_oracle_batch_rate(seconds=10.0, n_threads=None):
+    """The FP64 C oracle over images on all host cores (one image per thread at a time; ctypes
+    releases the GIL during each call): MP/s on mixed-size images of the batched workload."""
+    import concurrent.futures as cf
+    import oracle
+    from paper_2510_21100_gb300 import synth
+    n_threads = n_threads or os.cpu_count() or 1
+    sizes = synth.mixed_batch_sizes(4 * n_threads, 3)
+    imgs = [synth.low_light_image(w, h, seed=synth.seed_for(2, i)) for i, (w, h) in enumerate(sizes)]
+    p = oracle.Params()
+    oracle.enhance(imgs[0][:32, :32], p)
+    done_mp, t0 = 0.0, time.perf_counter()
+    with cf.ThreadPoolExecutor(n_threads) as ex:
+        while time.perf_counter() - t0 < seconds:
+            list(ex.map(lambda im: oracle.enhance(im, p), imgs))
+            done_mp += sum(im.shape[0] * im.shape[1] for im in imgs) / 1e6
+    return done_mp / (time.perf_counter() - t0), n_threads, len(imgs)
+
+
 def run_reference(a, rank, world):
     """The oracle as the reference arm: each step one bounded sample of the workload on the host."""
     if rank != 0:
@@ -204,10 +226,37 @@ def batched_leg(torch, hr, local, precision, n_imgs=512, steps=10, warmup=3, see
     ms = e0.elapsed_time(e1) / steps
     byts = 3 * 3 * mp * 1e6  # read for the histograms, read + write for the apply
     arith = {hr.PREC_FP64: "FP64", hr.PREC_DF64: "double-float"}[precision]
+    # the same images, one histretinex_enhance call each, round-robin on 4 streams (3 solve partitions)
+    single = hr.Context(hr.Params(precision=precision), device=local)
+    single.set_tuning(partitions=3)
+    sts = [torch.cuda.current_stream()] + [torch.cuda.Stream() for _ in range(3)]
+    for k in range(8):
+        single.enhance(ins[k], outs[k], stream=sts[k % 4])
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(sts[0])
+    for st in sts[1:]:
+        st.wait_event(f0)
+    reps = 3
+    for _ in range(reps):
+        for k in range(n_imgs):
+            single.enhance(ins[k], outs[k], stream=sts[k % 4])
+    for st in sts[1:]:
+        ev = torch.cuda.Event()
+        ev.record(st)
+        sts[0].wait_event(ev)
+    f1.record(sts[0])
+    torch.cuda.synchronize()
+    single.check()
+    ms_single = f0.elapsed_time(f1) / reps
+    single.close()
     return {"workload": f"{n_imgs} mixed uint8 images, {mp:.1f} MP per batch call, K=256, T=10, {arith} solve",
             "images": n_imgs,
             "MP": mp, "ms_per_batch": ms, "MP_per_s": mp / (ms / 1e3), "tuning": tune,
-            "gpu_launches_per_batch": (ctx.kernel_launches() - l0) / steps, "pipeline_GBps": byts / (ms / 1e3) / 1e9}
+            "gpu_launches_per_batch": (ctx.kernel_launches() - l0) / steps, "pipeline_GBps": byts / (ms / 1e3) / 1e9,
+            "same_images_single_calls": {"ms": ms_single, "MP_per_s": mp / (ms_single / 1e3),
+                                         "how": "one histretinex_enhance per image, round-robin on 4 streams, "
+                                                "3 solve partitions"}}
 
 
 def precision_leg(torch, hr, local, n_imgs=1024, steps=2, warmup=1):
@@ -292,13 +341,52 @@ def gamma_leg(hr, local):
             "rows": rows}
 
 
-def serving_leg(torch, hr, local, big_img, seconds=5.0, rate=400.0, seed=5):
-    """Continuous batching under Poisson arrivals (mean `rate` per second) of mixed-size 8-bit
-    requests: 70% of 0.3-2 MP, 25% of 2-8 MP, 5% of 7680x4320; 40 GB device budget.  The request
-    pool holds 6 + 3 generated images and the 7680x4320 workload image."""
+def ablation_leg(torch, hr, local, n=512, K=256, reps=5):
+    """The tcgen05 ablation of the reduced-precision form: Eq. 11 class totals of n images at K = 256
+    (reflectance and illumination histograms of synthetic low-light images: R = H_C(grad S) / N,
+    L = H_C(S) / N, the solve's first iterate) by the FP32 gather on the CUDA cores, the BF16 one-hot
+    GEMM on tcgen05 and its split hi + lo form; kernel time (mean of reps) and max relative error
+    against exact FP64 totals."""
+    import numpy as np
+    import oracle
+    from paper_2510_21100_gb300 import synth
+    R, L = np.zeros((n, K)), np.zeros((n, K))
+    base = [synth.low_light_image(320, 240, seed=synth.seed_for(7, i)) for i in range(16)]
+    for k in range(n):
+        img = np.ascontiguousarray(np.roll(base[k % 16], 7 * k, axis=1))
+        S, G = oracle.histograms(img, K)
+        R[k], L[k] = G / G.sum(), S / S.sum()
+    i = np.arange(K)[:, None]
+    j = np.arange(K)[None, :]
+    cm = ((2 * i * j + (K - 1)) // (2 * (K - 1))).ravel()
+    want = np.zeros((n, K))
+    for k in range(n):
+        np.add.at(want[k], cm, np.outer(R[k], L[k]).ravel())
+    dR = torch.from_numpy(R.astype(np.float32)).to(f"cuda:{local}")
+    dL = torch.from_numpy(L.astype(np.float32)).to(f"cuda:{local}")
+    nz = want > 0
+    out = {"workload": f"{n} images, K={K}: Eq. 11 class totals of the first iterate (one step of the solve)"}
+    for m, name in ((0, "fp32_gather_cuda_cores"), (1, "bf16_onehot_gemm_tcgen05"), (2, "bf16x2_split_onehot_gemm_tcgen05")):
+        hr.ablation_class_totals(dR, dL, m)
+        times, P = [], None
+        for _ in range(reps):
+            P, ms = hr.ablation_class_totals(dR, dL, m)
+            times.append(ms)
+        P = P.cpu().numpy().astype(np.float64)
+        out[name] = {"ms": sum(times) / len(times), "max_rel_err": float(np.max(np.abs(P[nz] - want[nz]) / want[nz])),
+                     "zero_pattern_exact": bool(np.array_equal(P != 0, nz))}
+    fp32 = out["fp32_gather_cuda_cores"]["ms"]
+    for name in ("bf16_onehot_gemm_tcgen05", "bf16x2_split_onehot_gemm_tcgen05"):
+        out[name]["time_vs_fp32_gather"] = out[name]["ms"] / fp32
+    out["tolerance_of_the_precision_form"] = 1e-4
+    return out
+
+
+def serving_pool(torch, synth, seed=5):
+    """The serving request mix: 70% 0.3-2 MP, 25% 2-8 MP (log-uniform area, aspect 4:3/16:9/3:2), 5%
+    the 7680x4320 workload image; a pool of 6 + 3 generated images and the large one."""
     import math
     import numpy as np
-    from paper_2510_21100_gb300 import serve, synth
     rng = np.random.default_rng(seed)
     pool, weights = [], []
     for band, (lo, hi), count, share in (("small", (0.3e6, 2e6), 6, 0.70), ("medium", (2e6, 8e6), 3, 0.25)):
@@ -308,18 +396,42 @@ def serving_leg(torch, hr, local, big_img, seconds=5.0, rate=400.0, seed=5):
             w = int(round(math.sqrt(area * ar))); h = int(round(area / w))
             pool.append(torch.from_numpy(synth.low_light_image(w, h, seed=synth.seed_for(5, len(pool)))).pin_memory())
             weights.append(share / count)
+    return pool, weights
+
+
+def serving_leg(torch, hr, local, big_img, seconds=5.0, rates=(400.0,), seed=5, warm_s=0.0, capacity_requests=1500):
+    """Continuous batching under Poisson arrivals of mixed-size 8-bit requests (40 GB device budget,
+    3 streams), at each rate in `rates` for `seconds` (statistics over the requests arriving after
+    warm_s); then capacity: `capacity_requests` requests all queued at once, served by the same
+    server, against the same requests sent one by one through histretinex_enhance on 4 streams."""
+    from paper_2510_21100_gb300 import serve, synth
+    pool, weights = serving_pool(torch, synth, seed)
     pool.append(torch.from_numpy(big_img).pin_memory())
     weights.append(0.05)
     srv = serve.Server(hr.Params(), budget_bytes=40 << 30, streams=3, max_batch=32, device=local)
-    warm = serve.poisson_requests(pool, rate, 0.5, seed=seed + 1, weights=weights)
-    srv.run(warm)
-    reqs = serve.poisson_requests(pool, rate, seconds, seed=seed, weights=weights)
-    st = srv.run(reqs)
+    srv.run(serve.poisson_requests(pool, rates[0], 0.5, seed=seed + 1, weights=weights))
+    out = {"workload": "Poisson arrivals, 70% 0.3-2 MP / 25% 2-8 MP / 5% 7680x4320, uint8, K=256, 40 GB budget, "
+                       "3 streams, continuous batching", "rates": []}
+    for rate in rates:
+        reqs = serve.poisson_requests(pool, rate, seconds, seed=seed, weights=weights)
+        st = srv.run(reqs)
+        row = st.summary()
+        row.update({"rate_req_per_s": rate, "seconds_offered": seconds,
+                    "offered_MP_per_s": sum(r.megapixels for r in reqs) / seconds})
+        if warm_s > 0:
+            row["after_warmup"] = serve.window_stats(reqs, warm_s)
+        out["rates"].append(row)
+    # capacity: every request queued at t = 0 (the same mix), served vs plain single-image calls
+    cap = serve.poisson_requests(pool, 1e6, capacity_requests / 1e6, seed=seed + 2, weights=weights)
+    for r in cap:
+        r.arrival = 0.0
+    sc = srv.run(cap).summary()
     srv.close()
-    out = st.summary()
-    out.update({"workload": f"Poisson {rate:g} req/s for {seconds:g} s, 70% 0.3-2 MP / 25% 2-8 MP / 5% 7680x4320, "
-                            "uint8, K=256, 40 GB budget, 3 streams", "offered_MP_per_s":
-                    sum(r.megapixels for r in reqs) / seconds})
+    pl = serve.plain_throughput(cap, hr.Params(), streams=4, partitions=3, device=local)
+    out["capacity"] = {"requests": len(cap), "MP": sum(r.megapixels for r in cap),
+                       "served_MP_per_s": sc["MP_per_s"], "served_p50_ms": sc["p50_ms"], "served_batches": sc["batches"],
+                       "plain_MP_per_s": pl["MP_per_s"], "plain": "one histretinex_enhance per request, 4 streams, "
+                       "3 solve partitions, host-to-device copy of each request included (as in the server)"}
     return out
 
 
@@ -453,14 +565,17 @@ def main():
     h_ms, s_ms, a_ms = stage
     stages = {"hist": h_ms, "solve": s_ms, "apply": a_ms}
     dom = max(stages, key=stages.get)
-    fp64_peak = 1250.0  # GFLOP/s: nominal GB300 FP64 from the profiling recipe (probe measured 1190-1200)
+    # FP64 peak: 2 DFMA per SM per clock x 152 SMs x 2.07 GHz x 2 flops = 1259 GFLOP/s; a throughput
+    # probe of dependent-free DFMA loops measured 1190-1200 on this GPU (no measured FP64 peak)
+    fp64_peak = 1200.0
     # the strip kernel runs when the image has at least 2 strips (512 x 4 pixels) per warp of a full grid
     hist_name = "hist_u8r_kernel" if -(-W // 512) * -(-H // 4) >= 2 * 16 * 152 else "hist_u8v_kernel"
     kern = {
         "hist": {"kernel": hist_name, "bound": "hbm", "achieved": hist_bytes / (h_ms / 1e3) / 1e9,
                  "peak": pk["hbm_gbs"], "unit": "GB/s", "peak_source": pk_src},
         "solve": {"kernel": "solve_kernel<double>", "bound": "alu", "achieved": solve_flops / (s_ms / 1e3) / 1e9,
-                  "peak": fp64_peak, "unit": "GFLOP/s", "peak_source": "nominal FP64 (recipe table)"},
+                  "peak": fp64_peak, "unit": "GFLOP/s",
+                  "peak_source": "builder's FP64 throughput probe (1190-1200 GFLOP/s measured)"},
         "apply": {"kernel": "apply_u8v_kernel", "bound": "hbm", "achieved": apply_bytes / (a_ms / 1e3) / 1e9,
                   "peak": pk["hbm_gbs"], "unit": "GB/s", "peak_source": pk_src},
     }
@@ -540,12 +655,21 @@ def main():
         line["batched_fp64"] = batched_leg(torch, hr, local, hr.PREC_FP64)
         torch.cuda.synchronize()
         torch.cuda.empty_cache()  # the legs' device buffers go back before the latency-sensitive one
-        line["serving"] = serving_leg(torch, hr, local, imgs[0])
+        if a.serving_seconds > 0:
+            line["serving"] = serving_leg(torch, hr, local, imgs[0], seconds=a.serving_seconds,
+                                          rates=tuple(float(x) for x in a.serving_rates.split(",")), warm_s=5.0)
+        else:
+            line["serving"] = serving_leg(torch, hr, local, imgs[0])
         line["precision"] = precision_leg(torch, hr, local)
         line["gamma_sensitivity"] = gamma_leg(hr, local)
+        line["precision_ablation"] = ablation_leg(torch, hr, local)
         rate, reps, shape = cpu_oracle_rate(imgs, seconds=10.0)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{reps} x full {shape[1]}x{shape[0]} image, single-threaded FP64 C oracle"}
+        brate, nthr, nimg = cpu_oracle_batch_rate(seconds=10.0)
+        line["cpu_baseline_all_cores"] = {"value": brate, "unit": UNIT, "cores": nthr, "kind": "oracle",
+                                          "sample": f"{nimg} mixed-size images of the batched workload, one per "
+                                                    f"host thread at a time, {nthr} threads, about 10 s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

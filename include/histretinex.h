@@ -275,6 +275,21 @@ hr_status histretinex_profile_solve(hr_ctx* ctx, int image, long long* ns, int* 
  * range beyond the form's; HR_ERR_CUDA if the launch fails. */
 hr_status histretinex_gradient_levels(int form, int K, int m2_first, int n, uint16_t* d_out, void* stream);
 
+/* Measured ablation of the reduced-precision form (north_star "Precision"), not part of the paper's
+ * method and not on the enhancement path: the Eq. 11 class totals P_n[k] = sum over the cells
+ * (i, j) of class k (index(i, j) = round(i j / (K - 1)), definition under Eq. 10) of R_n[i] L_n[j]
+ * (the count matrix of Eq. 6 without its 1/N) for n images at once.  method 0: an FP32 gather on the
+ * CUDA cores (a warp per class, FP32 fused multiply-adds); method 1: the class-sorted one-hot GEMM
+ * P = Z X on the tcgen05 tensor cores, Z the K x K^2 0/1 class matrix (exact in BF16), X the cell
+ * products rounded to BF16, FP32 accumulation in tensor memory; method 2: the same contraction over
+ * each product split into two BF16 numbers, hi + lo (two passes, about 16 bits kept).  d_R, d_L: device arrays of n x K
+ * FP32 values (image-major, level-indexed); d_P: device output, n x K FP32.  K must be 128 or 256,
+ * 1 <= n <= 4096.  The call allocates its own device buffers, waits for its kernels, and writes their
+ * device time in ms to *kernel_ms (may be NULL).  HR_ERR_TIMEOUT if a bounded wait of the tensor-core
+ * kernel gave up (its results are then not valid). */
+hr_status histretinex_ablation_class_totals(int K, int n, const float* d_R, const float* d_L, float* d_P, int method,
+                                           float* kernel_ms, void* stream);
+
 /* The SM partitioning single-image calls run with (see hr_tuning.partitions): *solve_parts = the
  * number of 16-SM solve partitions in use (0: unpartitioned, before the first call or where the
  * split is unavailable), *pixel_sms = the SMs of the pixel partition (all SMs when unpartitioned).

@@ -27,6 +27,7 @@ EXPORTS = (
     "histretinex_profile_solve", "histretinex_set_tuning", "histretinex_get_tuning",
     "histretinex_workspace_bytes", "histretinex_enhance_noalloc", "histretinex_reserve",
     "histretinex_enhance_host_many", "histretinex_gradient_levels", "histretinex_partition_info",
+    "histretinex_ablation_class_totals",
 )
 
 
@@ -106,6 +107,8 @@ def _lib():
         L.histretinex_reserve.restype = ctypes.c_int
         L.histretinex_partition_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
         L.histretinex_partition_info.restype = ctypes.c_int
+        L.histretinex_ablation_class_totals.argtypes = [i, i, vp, vp, vp, i, ctypes.POINTER(ctypes.c_float), vp]
+        L.histretinex_ablation_class_totals.restype = ctypes.c_int
         L.histretinex_gradient_levels.argtypes = [i, i, i, i, vp, vp]
         L.histretinex_gradient_levels.restype = ctypes.c_int
         L.histretinex_workspace_bytes.argtypes = [vp]
@@ -217,6 +220,21 @@ def gradient_levels(form: int, K: int, m2_first: int, n: int, stream=None):
     _check(_lib().histretinex_gradient_levels(form, K, m2_first, n, ctypes.c_void_p(out.data_ptr()),
                                               _stream_ptr(stream)), "histretinex_gradient_levels")
     return out
+
+
+def ablation_class_totals(R, L, method: int, stream=None):
+    """histretinex_ablation_class_totals: Eq. 11 class totals of n images (R, L: (n, K) float32 CUDA
+    tensors) by the FP32 gather (method 0), the BF16 one-hot GEMM on tcgen05 (method 1) or its split
+    hi + lo form (method 2); returns
+    (P as an (n, K) float32 tensor, kernel ms)."""
+    import torch
+    n, K = int(R.shape[0]), int(R.shape[1])
+    P = torch.empty((n, K), dtype=torch.float32, device=R.device)
+    ms = ctypes.c_float(0.0)
+    _check(_lib().histretinex_ablation_class_totals(K, n, ctypes.c_void_p(R.data_ptr()), ctypes.c_void_p(L.data_ptr()),
+                                                    ctypes.c_void_p(P.data_ptr()), method, ctypes.byref(ms),
+                                                    _stream_ptr(stream)), "histretinex_ablation_class_totals")
+    return P, ms.value
 
 
 class Context:

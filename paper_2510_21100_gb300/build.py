@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhistretinex.so")
-SOURCES = ["hr_api.cu", "hr_pixels.cu", "hr_solve.cu", "hr_static.cu", "hr_partition.cu"]
+SOURCES = ["hr_api.cu", "hr_pixels.cu", "hr_solve.cu", "hr_static.cu", "hr_partition.cu", "hr_ablation.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1001,6 +1001,29 @@ hr_status histretinex_stage_times(hr_ctx* c, double* ms, int* calls, int reset) 
 
 uint64_t histretinex_kernel_launches(const hr_ctx* c) { return c ? c->launches : 0; }
 
+hr_status histretinex_ablation_class_totals(int K, int n, const float* d_R, const float* d_L, float* d_P, int method,
+                                           float* kernel_ms, void* stream) {
+  if ((K != 128 && K != 256) || n < 1 || n > 4096 || !d_R || !d_L || !d_P || method < 0 || method > 2)
+    return HR_ERR_INVALID_ARG;
+  int dev = 0, sms = 0;
+  HR_CUDA(cudaGetDevice(&dev));
+  HR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  unsigned* d_status = nullptr;
+  HR_CUDA(cudaMalloc(&d_status, sizeof(unsigned)));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(unsigned), st);
+  hr_status s = e == cudaSuccess ? hr::ablation_class_totals(K, n, d_R, d_L, d_P, method, d_status, sms, st, kernel_ms)
+                                 : cuda_fail(e);
+  unsigned h = 0;
+  if (s == HR_OK) {
+    e = cudaMemcpy(&h, d_status, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) s = cuda_fail(e);
+  }
+  cudaFree(d_status);
+  if (s == HR_OK && (h & hr::kStTimeout)) s = HR_ERR_TIMEOUT;
+  return s;
+}
+
 hr_status histretinex_partition_info(const hr_ctx* c, int* solve_parts, int* pixel_sms) {
   if (!c || !solve_parts || !pixel_sms) return HR_ERR_INVALID_ARG;
   const bool on = c->part && c->tune.partitions == c->part_parts;  // (a changed count applies at the next call)

@@ -165,6 +165,12 @@ int partitions_pixel_sms(const Partitions* P);
 cudaError_t partitions_run(Partitions* P, int slot, cudaStream_t st, const StageFn& hist, const StageFn& solve,
                            const StageFn& apply);
 
+// Measured ablation: the Eq. 11 class totals of n images (R, L: n x K FP32, level-indexed) into
+// P (n x K FP32) by the FP32 gather on the CUDA cores (method 0) or the BF16 one-hot GEMM on the
+// tensor cores (method 1); *kernel_ms gets the kernels' device time.
+hr_status ablation_class_totals(int K, int n, const float* d_R, const float* d_L, float* d_P, int method,
+                                unsigned* d_status, int sms, cudaStream_t st, float* kernel_ms);
+
 // Geometry of the pixel passes: tiles of kTileW x kTileH pixels.
 constexpr int kTileW = 128;
 constexpr int kTileH = 32;

@@ -54,6 +54,57 @@ class ServeStats:
                 "max_batch": self.max_batch}
 
 
+def window_stats(requests, start: float, end: float | None = None) -> dict:
+    """Latency percentiles and served MP/s of the requests that arrived in [start, end) of a run (the
+    first seconds of a run, while streams and caches warm up, are left out this way)."""
+    sel = [r for r in requests if r.arrival >= start and (end is None or r.arrival < end)]
+    if not sel:
+        return {"requests": 0}
+    lat = sorted((r.done - r.arrival) * 1e3 for r in sel)
+    pick = lambda q: lat[min(len(lat) - 1, max(0, int(math.ceil(q / 100.0 * len(lat))) - 1))]
+    span = max(r.done for r in sel) - min(r.arrival for r in sel)
+    return {"requests": len(sel), "window_s": span, "MP_per_s": sum(r.megapixels for r in sel) / span,
+            "p50_ms": pick(50), "p99_ms": pick(99)}
+
+
+def plain_throughput(requests, params: hr.Params | None = None, streams: int = 4, partitions: int | None = None,
+                     device: int = 0) -> dict:
+    """The plain form on the same requests: each image copied to the device and enhanced by its own
+    histretinex_enhance call, the calls going round-robin to `streams` streams of one context (calls
+    on different streams overlap on the device), all issued at once.  Returns MP/s over the
+    makespan (host issue to the last completion)."""
+    import torch
+    ctx = hr.Context(params or hr.Params(), device=device)
+    if partitions is not None:
+        ctx.set_tuning(partitions=partitions)
+    sts = [torch.cuda.Stream(device=device) for _ in range(streams)]
+    warm = requests[: min(8, len(requests))]
+    for k, r in enumerate(warm):
+        with torch.cuda.stream(sts[k % streams]):
+            d = hr.to_device_aligned(r.image, f"cuda:{device}")
+            ctx.enhance(d, hr.aligned_empty(int(d.shape[0]), int(d.shape[1]), d.dtype, f"cuda:{device}"),
+                        stream=sts[k % streams])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    outs = []
+    for k, r in enumerate(requests):
+        st = sts[k % streams]
+        with torch.cuda.stream(st):
+            d = hr.to_device_aligned(r.image, f"cuda:{device}")
+            o = hr.aligned_empty(int(d.shape[0]), int(d.shape[1]), d.dtype, f"cuda:{device}")
+            ctx.enhance(d, o, stream=st)
+            outs.append(o)
+        if len(outs) > 4 * streams:  # keep device memory bounded: results are dropped as they complete
+            outs.pop(0)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    ctx.check()
+    ctx.close()
+    mp = sum(r.megapixels for r in requests)
+    return {"requests": len(requests), "seconds": el, "MP_per_s": mp / el, "streams": streams,
+            "partitions": partitions}
+
+
 class Server:
     def __init__(self, params: hr.Params | None = None, budget_bytes: int = 40 << 30, streams: int = 3,
                  max_batch: int = 64, device: int = 0):
