@@ -26,9 +26,9 @@ UNIT = "MP/s"
 
 
 # DRAM bytes (read + write) per launch of each kernel at 7680x4320, K = 256, from one ncu capture
-# of the current kernels (profiles/*_7680x4320.md); the apply's writes still in L2 when the
-# kernel ends are not counted there.
-PROFILED_DRAM_BYTES = {"hist_u8r_kernel": 107_502_592, "solve_kernel<double>": 210_688, "apply_u8v_kernel": 147_325_440}
+# of the current kernels (profiles/pipeline_7680x4320_launches.md); the apply's writes still in L2
+# when the kernel ends are not counted there.
+PROFILED_DRAM_BYTES = {"hist_u8r_kernel": 105_511_680, "solve_kernel<double>": 219_136, "apply_u8v_kernel": 147_895_808}
 
 
 def parse():
