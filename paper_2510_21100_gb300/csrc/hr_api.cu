@@ -327,7 +327,6 @@ cudaError_t enqueue_stages(hr_ctx* c, const Group& g, int elem_bytes, bool fast_
                            cudaEvent_t after_hist = nullptr) {
   const int K = c->p.K, n = g.tab.n;
   const int pdl = c->tune.pdl;  // bit 0: histogram pass, bit 1: solve, bit 2: apply pass
-  const bool debug = (c->p.flags & HR_FLAG_DEBUG_OUT) != 0;
   cudaError_t e;
   // zero H_C(S) and H_C(grad S) of every slot used (S and G are adjacent at the slot start)
   if (zero) {

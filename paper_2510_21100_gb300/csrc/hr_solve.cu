@@ -828,16 +828,24 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     for (int a = aA + warp; a < aB; a += NW) {  // own rows, a warp each
       const int i = RI[a];
       const uint16_t* jr = A.jstart1 + (size_t)i * (K + 1);  // js1(i, k), k <= K (entry K holds K)
-      // classes of the first and last support column: k0 + 1 = #{k : js1(i, k) <= jmin}, likewise
-      // k1 for jmax (js1 grows with k; boundaries read 32 at a time, counted by ballots)
+      // classes of the first and last support column: k0 + 1 = #{k < K : js1(i, k) <= jmin}, likewise
+      // k1 for jmax.  js1 grows with k and js1(i, 0) = 0, so each count is found by a 32-ary search:
+      // the lanes probe 32 boundaries stride apart, a ballot counts those within the column, the
+      // search continues from the last of them with a stride 32 times smaller (three rounds at
+      // K = 4096, one for K <= 32), both counts side by side.
       int c0 = 0, c1 = 0;
-      for (int kb = 0; kb < K; kb += 32) {
-        const int k = kb + lane;
-        const int v = k < K ? (int)jr[k] : K + 1;
-        const unsigned m1 = __ballot_sync(FULL, v <= jmax);
-        c0 += __popc(__ballot_sync(FULL, v <= jmin));
-        c1 += __popc(m1);
-        if (m1 != FULL) break;  // the boundaries have passed the last support column
+      {
+        int s0 = 0, s1 = 0, stride = 1;
+        while (stride * 32 < K) stride *= 32;
+        for (;;) {
+          const int ka = s0 + lane * stride, kb = s1 + lane * stride;
+          const int m0 = __popc(__ballot_sync(FULL, ka < K && (int)jr[ka] <= jmin));  // >= 1: the probe at s0
+          const int m1 = __popc(__ballot_sync(FULL, kb < K && (int)jr[kb] <= jmax));
+          if (stride == 1) { c0 = s0 + m0; c1 = s1 + m1; break; }
+          s0 += (m0 - 1) * stride;
+          s1 += (m1 - 1) * stride;
+          stride /= 32;
+        }
       }
       const int k0 = c0 - 1, k1 = min(c1 - 1, i);  // (index_1 never exceeds i: a_j <= 1)
       if (lane == 0) { rk0[a] = (unsigned)k0; rk1[a] = (unsigned)k1; }
