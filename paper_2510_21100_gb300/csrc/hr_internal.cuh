@@ -175,7 +175,8 @@ hr_status ablation_class_totals(int K, int n, const float* d_R, const float* d_L
 constexpr int kTileW = 128;
 constexpr int kTileH = 32;
 inline int tiles_of(int W, int H) { return ((W + kTileW - 1) / kTileW) * ((H + kTileH - 1) / kTileH); }
-// Units of the 8-bit histogram pass: strips kStripW pixels wide and kBandH rows high, one warp each.
+// Units of the 8-bit strip histogram pass: strips kStripW pixels wide and kBandH rows high, counted
+// column by column within an image; the kernel deals their rows out to its warps in equal runs.
 constexpr int kStripW = 512;
 constexpr int kBandH = 4;
 inline int strips_of(int W, int H) { return ((W + kStripW - 1) / kStripW) * ((H + kBandH - 1) / kBandH); }

@@ -199,18 +199,9 @@ __global__ void __launch_bounds__(kThreads) apply_kernel(const ImgTab tab, int t
 // ------------------------------------------------------------------------------------------------
 // 8-bit fast paths (rows 16-byte aligned).
 //
-// Histogram pass: one warp walks one strip of kStripW x kBandH pixels.  Lane l owns the 16
-// pixels [x0 + 16 l, x0 + 16 l + 16) of the strip's rows, so the warp reads 1536 contiguous bytes
-// per row and the warps of a CTA, dealt consecutive strips, read whole image rows together (DRAM
-// pages are read through; narrow tiles spread over many rows reached barely half the bandwidth).
-// Each lane copies its 48 bytes of the ten rows y0 - 1 .. y0 + 8 (clamped to the image: replicate
-// border) into its own shared-memory ring kRing rows ahead of use with asynchronous copies.
-// V = max(r, g, b) is kept as packed 16-bit pairs, even and odd pixels apart, so one 32-bit add
-// forms a Sobel partial sum of two pixels; the columns left and right of a lane's 16 pixels come
-// from the neighbouring lanes by shuffles, or at the strip edge from one 4-byte copy.  The squared
-// magnitude of each pair is unpacked with a sign extension and a high multiply.  Counts go to
-// per-warp shared histograms by shared-memory reductions; each CTA deals its contiguous range of
-// strips out to its warps through a shared counter.
+// Histogram pass, large images and batches: the rolling strip kernel below.  Lane l of a warp owns
+// the 16 pixels [x0 + 16 l, x0 + 16 l + 16) of a strip's rows, so the warp reads 1536 contiguous
+// bytes per row.  Smaller launches: the staged-tile kernel further down.
 //
 // Apply pass: 16 pixels (48 bytes, three 16-byte vectors) per thread each way.
 // ------------------------------------------------------------------------------------------------
@@ -223,80 +214,15 @@ constexpr int kHT = kHW * 32;
 #define HR_STRIP_MIN_FACTOR 2  // strips per warp from which one image takes the strip kernel
 #endif
 constexpr int kHBins = 256;     // per-warp histogram stride (the 8-bit pass has K <= 256)
-constexpr int kRing = 3;        // rows in flight per warp (3 measured faster than 4 with 4-row bands)
-constexpr int kSlot = 32 * 48;  // bytes of one ring slot of a warp: 48 per lane
 
-// Shared memory of the fast histogram pass: per warp its two histograms, then per warp a ring
-// of kRing row slots (the strip's 1536 bytes of a row: 48 bytes per lane) and of kRing neighbour
-// words per lane.
-constexpr size_t kHistSmem = (size_t)kHW * (4 * kHBins * 4 + kRing * kSlot + kRing * 32 * 4);
-
-// One row of V around a lane's 16 pixels.
-struct VRow {
-  unsigned e[4], o[4];  // V of pixels (4w, 4w+2) and (4w+1, 4w+3) as 16-bit pairs, w = 0..3
-  unsigned l, r;        // high half of l: V of the pixel left of the 16; low half of r: the one right
-};
-
-// Per-lane geometry of the current strip and the lane's view of the warp's ring.
-struct LaneTile {
-  const uint8_t* in;
-  long long pitch;
-  int W, H;
-  int x0, xc, cnt;      // strip origin column, first column of the lane, W - xc
-  int lx;
-  unsigned char* ring;  // the lane's 48 bytes in slot 0 (slot s at + s * kSlot)
-  unsigned char* slot0; // the warp's slot 0
-  unsigned* nbr;        // the lane's neighbour word in slot 0 (slot s at + s * 32)
-};
-
-__device__ __forceinline__ const uint8_t* row_ptr(const LaneTile& g, int y) {
-  return g.in + (long long)clampi(y, 0, g.H - 1) * g.pitch;
-}
-
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
-}
 // 16-byte copy of which only the first `nb` (0..16) bytes are read; the rest is zero-filled.
 __device__ __forceinline__ void cp_async16z(void* smem_dst, const void* gsrc, int nb) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "r"(nb) : "memory");
 }
-__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-// Starts the copies of row y into ring slot `slot` (one commit group per call; empty when
-// `live` is false): the strip's 1536 bytes of the row as 96 chunks of 16 bytes, chunk c by lane
-// c mod 32, so each copy instruction of the warp covers 512 contiguous bytes (the bytes past the
-// image's last pixel are zero-filled), and the 4-byte neighbour words of lanes 0 and 31.  Lanes
-// read chunks other lanes copied: a __syncwarp after the wait_group orders copies and reads, one
-// before the next copies into a slot orders the reads before them.
-__device__ __forceinline__ void issue_row(const LaneTile& g, int slot, int y, bool live) {
-  if (live) {
-    const uint8_t* row = row_ptr(g, y);
-    unsigned char* dst = g.slot0 + slot * kSlot;
-    const int b0 = 3 * g.x0, rowbytes = 3 * g.W;
-    if (b0 + kSlot <= rowbytes) {
-#pragma unroll
-      for (int i = 0; i < 3; ++i) cp_async16(dst + 16 * (g.lx + 32 * i), row + b0 + 16 * (g.lx + 32 * i));
-    } else {
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const int off = 16 * (g.lx + 32 * i);
-        const int b = min(max(rowbytes - (b0 + off), 0), 16);
-        cp_async16z(dst + off, b > 0 ? (const void*)(row + b0 + off) : (const void*)row, b);
-      }
-    }
-    if (g.lx == 0 && g.x0 > 0) cp_async4(g.nbr + slot * 32, row + 3 * g.x0 - 4);
-    else if (g.lx == 31 && g.x0 + kStripW + 2 <= g.W) cp_async4(g.nbr + slot * 32, row + 3 * (g.x0 + kStripW));
-  }
-  cp_async_commit();
-}
 
 // V of two pixels as 16-bit pairs from the 12 bytes of four pixels: a = R0 G0 B0 R1,
 // b = G1 B1 R2 G2, c = B2 R3 G3 B3.  Every operand of one 3-way max carries the same filler
@@ -306,189 +232,292 @@ __device__ __forceinline__ void vpairs(unsigned a, unsigned b, unsigned c, unsig
   o = __vimax3_u16x2(__byte_perm(a, c, 0x4543), __byte_perm(b, c, 0x4640), __byte_perm(b, c, 0x4741)) & 0x00ff00ffu;
 }
 
-__device__ __forceinline__ unsigned max3b(unsigned w, int s0) {  // max of bytes s0, s0+1, s0+2 of w
-  return max(max((w >> (8 * s0)) & 0xffu, (w >> (8 * s0 + 8)) & 0xffu), (w >> (8 * s0 + 16)) & 0xffu);
+// ------------------------------------------------------------------------------------------------
+// Rolling strip histogram pass (8-bit, rows 16-byte aligned).  The strips of kStripW pixels are cut
+// into strip rows, column by column and image after image; warp w of the grid takes the w-th of
+// equal contiguous ranges of that sequence, so a warp walks long runs down one strip column,
+// building each V row once (plus two halo rows per run), and all warps finish together.  The warp
+// copies every row it needs -- the strip's 1536 bytes and the 16-byte chunks on either side, which
+// hold the neighbour pixels -- into its ring of kSRing row slots with asynchronous copies, kSRing
+// rows ahead of use.  Building a row counts its V levels into H_C(S) and converts V to half-
+// precision pairs.  The Sobel sums (integers of magnitude at most 4 * 255 = 1020, exact in half
+// precision) run on pairs of pixels, and each pixel's squared magnitude (at most 2 * 1020^2 < 2^24)
+// is formed exactly in FP32 by two fused multiply-adds with half-precision inputs.
+// ------------------------------------------------------------------------------------------------
+constexpr int kSRing = 4;                            // row slots per warp (a power of two)
+constexpr int kSSlot = 16 + 3 * kStripW + 16;        // left chunk, the strip's row, right chunk
+// A warp's two histogram copies (even and odd lanes), each H_C(S) then H_C(grad S), the second
+// copy 16 words further on, so the two copies' counts of one level fall in different banks (24%
+// fewer shared-memory wavefronts of the counts at 7680x4320).
+constexpr int kHCopyWords = 2 * kHBins + 16;
+constexpr size_t kRollSmem = (size_t)kHW * (2 * kHCopyWords * 4 + kSRing * kSSlot);
+constexpr unsigned kHalfMagic = 0x64006400u;         // half 1024 in each half: 1024 + v for v < 1024
+constexpr unsigned kHalfMinus1024 = 0xE400E400u;     // half -1024 in each half
+constexpr unsigned kHalfTwo = 0x40004000u;           // half 2 in each half
+
+__device__ __forceinline__ unsigned hadd2(unsigned a, unsigned b) {
+  unsigned d;
+  asm("add.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned hsub2(unsigned a, unsigned b) {
+  unsigned d;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned hfma2(unsigned a, unsigned b, unsigned c) {
+  unsigned d;
+  asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+// Shared-memory count without a compiler memory barrier: the histograms are read only after the
+// warp and block barriers at a warp's image change and at the kernel's end.
+__device__ __forceinline__ void red_sh(unsigned addr) { asm volatile("red.shared.add.u32 [%0], 1;\n" ::"r"(addr)); }
+__device__ __forceinline__ void cp_async16s(unsigned dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16zs(unsigned dst, const void* src, int nb) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(nb) : "memory");
 }
 
-// V row of one lane from ring slot `slot` (row y); all lanes of the warp call it together.
-// Positions right of the image's last pixel hold zeros, except the first one, which holds the
-// replica of the last pixel (replicate border).
-template <bool kEdge, bool kClamp>
-__device__ __forceinline__ VRow build_row(const LaneTile& g, int slot, int y, unsigned kk, bool& bad) {
-  VRow v;
-  const unsigned char* qb = g.ring + slot * kSlot;
-  {
-    const uint4* q = reinterpret_cast<const uint4*>(qb);
-    const uint4 a = q[0], b = q[1], c = q[2];
-    vpairs(a.x, a.y, a.z, v.e[0], v.o[0]);
-    vpairs(a.w, b.x, b.y, v.e[1], v.o[1]);
-    vpairs(b.z, b.w, c.x, v.e[2], v.o[2]);
-    vpairs(c.y, c.z, c.w, v.e[3], v.o[3]);
-  }
-  if (kEdge && g.cnt <= 0) {  // lane right of the image: nothing was copied, nothing is counted
+// Gradient level of a squared magnitude m2 held exactly in FP32: the nearest integer to sqrt(m2)
+// clipped to K - 1, as 0x4B000000 + level in the result's bits.  Clipping m2 at K^2 - K first gives
+// the same level and keeps m2 below 2^23; sqrt.approx (flush-to-zero: no m2 here is subnormal) is
+// within 2^-22 relative of sqrt(m2) there, well inside the distance 1/(4 sqrt(m2) + 2) from sqrt(m2)
+// to the nearest half integer, so the round-to-nearest add of 2^23 yields the exact level.
+__device__ __forceinline__ unsigned grad_bits_f(float m2, float mclipf) {
+  const float f = fminf(m2, mclipf);
+  float s;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(f));
+  return __float_as_uint(__fadd_rn(s, 8388608.0f));
+}
+
+// Squared magnitudes of the two pixels of half-precision pairs (gx, gy), exact in FP32.
+__device__ __forceinline__ void m2_pair(unsigned gx, unsigned gy, float& mlo, float& mhi) {
+  asm("{\n.reg .f16 xl, xh, yl, yh;\n.reg .f32 t, u;\n"
+      "mov.b32 {xl, xh}, %2;\nmov.b32 {yl, yh}, %3;\n"
+      "fma.rn.f32.f16 t, yl, yl, %4;\nfma.rn.f32.f16 %0, xl, xl, t;\n"
+      "fma.rn.f32.f16 u, yh, yh, %4;\nfma.rn.f32.f16 %1, xh, xh, u;\n}\n"
+      : "=f"(mlo), "=f"(mhi)
+      : "r"(gx), "r"(gy), "f"(0.0f));
+}
+
+// V row of one lane as half-precision pairs.
+struct HRow {
+  unsigned e[4], o[4];  // pixels (4w, 4w + 2) and (4w + 1, 4w + 3), w = 0..3
+  unsigned l, r;        // high half of l: the pixel left of the 16; low half of r: the one right
+};
+
+// A lane's constants for one run of rows down one strip column.
+struct SegLane {
+  const uint8_t* in;
+  long long pitch;
+  int H;
+  int goff;         // byte offset in a row of the lane's first 16-byte chunk (3 x0 + 16 lane)
+  int xoff;         // byte offset in a row of the lane's extra chunk (lane 0: left, lane 1: right)
+  int xbytes;       // bytes the extra chunk reads (0: none)
+  unsigned sxo;     // slot offset of the extra chunk
+  unsigned soff;    // slot offset of the lane's first copied chunk: 16 (lane + 1)
+  unsigned roff;    // slot offset of the lane's 48 bytes (pixels x0 + 16 lane ..): 16 + 48 lane
+  unsigned nbo;     // slot offset of the neighbour word: 12 (lane 0) or 16 + 1536 (the others)
+  unsigned sel0, sel1, sel2;  // byte selectors of the neighbour pixel's three channels
+  int cnt;          // pixels of the lane inside the image: W - (x0 + 16 lane)
+  int rowbytes;     // 3 W
+  bool lane0, lane31, left_nb, right_nb, use_nb;
+};
+
+// Copies row y (clamped: replicate border) into the slot at shared address `slot`: lane l copies
+// the strip's 16-byte chunks l, l + 32 and l + 64 (so each copy instruction of the warp covers 512
+// contiguous bytes) to slot offsets 16 + 16 c, lane 0 the left chunk to offset 0 and lane 1 the
+// right chunk to offset 16 + 1536; lanes read their own 48 bytes after the wait and a __syncwarp.
+// One commit group per call, empty when `live` is false.  Edge runs read only the bytes inside the row (the
+// rest of each chunk is zero-filled).
+template <bool kEdge>
+__device__ __forceinline__ void roll_issue(const SegLane& s, unsigned slot, int y, bool live) {
+  if (live) {
+    const uint8_t* row = s.in + (long long)clampi(y, 0, s.H - 1) * s.pitch;
+    const uint8_t* src = row + s.goff;
+    const unsigned dst = slot + s.soff;
+    if (!kEdge) {
+      cp_async16s(dst, src);
+      cp_async16s(dst + 512, src + 512);
+      cp_async16s(dst + 1024, src + 1024);
+    } else {
 #pragma unroll
-    for (int w = 0; w < 4; ++w) v.e[w] = v.o[w] = 0u;
+      for (int i = 0; i < 3; ++i) {
+        const int b = min(max(s.rowbytes - (s.goff + 512 * i), 0), 16);
+        cp_async16zs(dst + 512 * i, b > 0 ? (const void*)(src + 512 * i) : (const void*)row, b);
+      }
+    }
+    if (s.xbytes > 0) cp_async16zs(slot + s.sxo, row + s.xoff, s.xbytes);
+  }
+  cp_async_commit();
+}
+
+// Builds one V row from a slot; counts its levels into H_C(S) when `count` is set.
+template <bool kEdge, bool kClamp>
+__device__ __forceinline__ void roll_build(HRow& v, const SegLane& s, const unsigned char* slotp, bool count,
+                                           unsigned hs_sh, unsigned kk, bool& bad) {
+  unsigned u[8];  // u[2w] = pixels (4w, 4w + 2), u[2w + 1] = pixels (4w + 1, 4w + 3): V as 16-bit pairs
+  {
+    const uint4* q = reinterpret_cast<const uint4*>(slotp + s.roff);
+    const uint4 a = q[0], b = q[1], c = q[2];
+    vpairs(a.x, a.y, a.z, u[0], u[1]);
+    vpairs(a.w, b.x, b.y, u[2], u[3]);
+    vpairs(b.z, b.w, c.x, u[4], u[5]);
+    vpairs(c.y, c.z, c.w, u[6], u[7]);
+  }
+  if (kEdge && s.cnt <= 0) {
+#pragma unroll
+    for (int w = 0; w < 8; ++w) u[w] = 0u;
   }
   if (kClamp) {  // K < 256: levels above K - 1 are a range error, clamped so counting stays in bounds
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      const unsigned ce = __vimin3_u16x2(v.e[w], kk, kk), co = __vimin3_u16x2(v.o[w], kk, kk);
-      bad |= (ce != v.e[w]) | (co != v.o[w]);
-      v.e[w] = ce;
-      v.o[w] = co;
+    for (int w = 0; w < 8; ++w) {
+      const unsigned c = __vimin3_u16x2(u[w], kk, kk);
+      bad |= c != u[w];
+      u[w] = c;
     }
   }
-  // neighbour columns: from the adjacent lanes of the lane row, else from the neighbour word
-  v.l = __shfl_up_sync(0xffffffffu, v.o[3], 1);
-  v.r = __shfl_down_sync(0xffffffffu, v.e[0], 1);
-  if (g.lx == 0) {
-    unsigned lv = v.e[0] & 0xffffu;  // x0 == 0: replicate pixel 0
-    if (g.x0 > 0) lv = max3b(g.nbr[slot * 32], 1);
-    if (kClamp) { bad |= lv > (kk & 0xffffu); lv = min(lv, kk & 0xffffu); }
-    v.l = lv << 16;
-  }
-  if (g.xc + 16 >= g.W) {  // the lane holds the image's last pixel: replicate it to its right
-    if (!kEdge || g.cnt >= 16) {
-      v.r = v.o[3] >> 16;
-    } else if (g.cnt > 0) {
-      const unsigned char* lp = qb + 3 * (g.cnt - 1);
-      unsigned vlast = max(max((unsigned)lp[0], (unsigned)lp[1]), (unsigned)lp[2]);
-      if (kClamp) vlast = min(vlast, kk & 0xffffu);
-      v.r = vlast;
+  if (count) {
 #pragma unroll
-      for (int w = 0; w < 4; ++w) {  // pixel cnt (zero-filled) becomes the replica
-        if (4 * w == g.cnt) v.e[w] = (v.e[w] & 0xffff0000u) | vlast;
-        if (4 * w + 2 == g.cnt) v.e[w] = (v.e[w] & 0x0000ffffu) | (vlast << 16);
-        if (4 * w + 1 == g.cnt) v.o[w] = (v.o[w] & 0xffff0000u) | vlast;
-        if (4 * w + 3 == g.cnt) v.o[w] = (v.o[w] & 0x0000ffffu) | (vlast << 16);
-      }
+    for (int w = 0; w < 4; ++w) {
+      const bool on0 = !kEdge || 4 * w < s.cnt, on1 = !kEdge || 4 * w + 1 < s.cnt;
+      const bool on2 = !kEdge || 4 * w + 2 < s.cnt, on3 = !kEdge || 4 * w + 3 < s.cnt;
+      if (on0) red_sh(hs_sh + ((u[2 * w] & 0xffffu) << 2));
+      if (on2) red_sh(hs_sh + (u[2 * w] >> 14));  // 0x00VV00WW >> 14 = VV << 2
+      if (on1) red_sh(hs_sh + ((u[2 * w + 1] & 0xffffu) << 2));
+      if (on3) red_sh(hs_sh + (u[2 * w + 1] >> 14));
     }
-  } else if (g.lx == 31) {
-    unsigned rv;
-    if (g.x0 + kStripW + 2 <= g.W) {
-      rv = max3b(g.nbr[slot * 32], 0);
-    } else {  // the right neighbour is the image's last pixel
-      const uint8_t* p = row_ptr(g, y) + 3 * (g.x0 + kStripW);
-      rv = max(max((unsigned)p[0], (unsigned)p[1]), (unsigned)p[2]);
+  }
+  if (kEdge && s.cnt > 0 && s.cnt < 16) {  // the pixel right of the image's last one replicates it
+    const unsigned char* lp = slotp + s.roff + 3 * (s.cnt - 1);
+    unsigned vl = max(max((unsigned)lp[0], (unsigned)lp[1]), (unsigned)lp[2]);
+    if (kClamp) vl = min(vl, kk & 0xffffu);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      if (4 * w == s.cnt) u[2 * w] = (u[2 * w] & 0xffff0000u) | vl;
+      if (4 * w + 2 == s.cnt) u[2 * w] = (u[2 * w] & 0x0000ffffu) | (vl << 16);
+      if (4 * w + 1 == s.cnt) u[2 * w + 1] = (u[2 * w + 1] & 0xffff0000u) | vl;
+      if (4 * w + 3 == s.cnt) u[2 * w + 1] = (u[2 * w + 1] & 0x0000ffffu) | (vl << 16);
     }
-    if (kClamp) { bad |= rv > (kk & 0xffffu); rv = min(rv, kk & 0xffffu); }
-    v.r = rv;
   }
-  return v;
-}
-
-__device__ __forceinline__ void red_shared(unsigned addr) {
-  asm volatile("red.shared.add.u32 [%0], 1;\n" ::"r"(addr) : "memory");
-}
-
-// Counts one pixel: V level v into H_C(S); its gradient level, the nearest integer to sqrt(m2)
-// clipped to K - 1, into H_C(grad S).  Clipping m2 at K^2 - K first gives the same level, keeps
-// m2 below 2^23 so float(m2) is the magic-number conversion, and sqrt.approx is within 2^-19
-// relative of sqrt(m2) there, well inside the distance 1/(4 sqrt(m2) + 2) from sqrt(m2) to the
-// nearest half integer, so the round-to-nearest add of 2^23 yields the exact level
-// (0x4B000000 + level in the float's bits; hg_adj absorbs the 0x4B000000).
-__device__ __forceinline__ unsigned strip_grad_bits(int m2, int mclip) {
-  const int m2c = min(m2, mclip);
-  const float f = __fsub_rn(__int_as_float(0x4B000000 | m2c), 8388608.0f);
-  float s;
-  asm("sqrt.approx.f32 %0, %1;" : "=f"(s) : "f"(f));
-  return __float_as_uint(__fadd_rn(s, 8388608.0f));
-}
-__device__ __forceinline__ void count_px(int m2, unsigned v, int mclip, unsigned hs_sh, unsigned hg_adj, bool on) {
-  const unsigned gb = strip_grad_bits(m2, mclip);
-  if (on) {
-    red_shared(hg_adj + (gb << 2));
-    red_shared(hs_sh + (v << 2));
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    v.e[w] = hadd2(u[2 * w] | kHalfMagic, kHalfMinus1024);
+    v.o[w] = hadd2(u[2 * w + 1] | kHalfMagic, kHalfMinus1024);
+  }
+  // neighbour columns: from the adjacent lanes, at the strip's ends from the neighbour chunks, at
+  // the image's ends the replicated edge pixel
+  unsigned nbv;
+  {
+    const unsigned nbw = *reinterpret_cast<const unsigned*>(slotp + s.nbo);
+    nbv = __vimax3_u16x2(__byte_perm(nbw, 0u, s.sel0), __byte_perm(nbw, 0u, s.sel1), __byte_perm(nbw, 0u, s.sel2));
+    if (kClamp) {
+      bad |= s.use_nb && nbv > (kk & 0xffffu);
+      nbv = min(nbv, kk & 0xffffu);
+    }
+    nbv = hadd2(nbv | kHalfMagic, kHalfMinus1024);  // low half: the neighbour's V
+  }
+  const unsigned up = __shfl_up_sync(0xffffffffu, v.o[3], 1);
+  const unsigned dn = __shfl_down_sync(0xffffffffu, v.e[0], 1);
+  v.l = s.lane0 ? __byte_perm(s.left_nb ? nbv : v.e[0], 0u, 0x1010) : up;
+  if (kEdge) {
+    v.r = s.cnt == 16 ? __byte_perm(v.o[3], 0u, 0x3232) : ((s.lane31 && s.right_nb) ? nbv : dn);
+  } else {
+    v.r = s.lane31 ? (s.right_nb ? nbv : __byte_perm(v.o[3], 0u, 0x3232)) : dn;
   }
 }
 
-// Two pixels from packed Sobel components: each 32-bit word is HI * 65536 + LO with LO, HI the
-// signed components of the low and high pixel (exact: the packed adds never carry out of a
-// half by more than the borrow this form absorbs).
-__device__ __forceinline__ void count_pair(int gx, int gy, unsigned vpair, int p0, int lim, int mclip,
-                                           unsigned hs_sh, unsigned hg_adj) {
-  const int ax = (int)(short)gx, ay = (int)(short)gy;
-  const int m2a = ax * ax + ay * ay;
-  const int dx = gx - ax, dy = gy - ay;
-  const int m2b = __mulhi(dx, dx) + __mulhi(dy, dy);
-  count_px(m2a, vpair & 0xffffu, mclip, hs_sh, hg_adj, p0 < lim);
-  count_px(m2b, vpair >> 16, mclip, hs_sh, hg_adj, p0 + 2 < lim);
-}
-
-// Separable Sobel (gx: right minus left column of [1 2 1]^T-weighted sums; gy: bottom minus top
-// row of [1 2 1]-weighted sums) and counting for the output row M between rows T and B.
-__device__ __forceinline__ void count_row(const VRow& T, const VRow& M, const VRow& B, int lim, int mclip,
-                                          unsigned hs_sh, unsigned hg_adj) {
-  // column sums cs = T + 2 M + B and differences dd = B - T + 256 per half (in [1, 511]), formed
-  // word by word as the window over the four pairs moves right
-  auto cs = [](unsigned t, unsigned m, unsigned b) { return t + b + 2u * m; };
-  auto dd = [](unsigned t, unsigned b) { return b - t + 0x01000100u; };
-  unsigned csOp = cs(T.l, M.l, B.l), ddOp = dd(T.l, B.l);  // odd pair left of pair 0 (high half: x - 1)
+// Sobel gradient of the output row M between rows T and B, counted into H_C(grad S).
+template <bool kEdge>
+__device__ __forceinline__ void roll_sobel(const HRow& T, const HRow& M, const HRow& B, int cnt, float mclipf,
+                                           unsigned hg_adj) {
+  auto cs = [](unsigned t, unsigned m, unsigned b) { return hadd2(hfma2(m, kHalfTwo, t), b); };
+  auto dd = [](unsigned t, unsigned b) { return hsub2(b, t); };
+  unsigned csOp = cs(T.l, M.l, B.l), ddOp = dd(T.l, B.l);  // high half: the pixel left of the 16
   unsigned csEc = cs(T.e[0], M.e[0], B.e[0]), ddEc = dd(T.e[0], B.e[0]);
 #pragma unroll
   for (int w = 0; w < 4; ++w) {
     const unsigned csOc = cs(T.o[w], M.o[w], B.o[w]), ddOc = dd(T.o[w], B.o[w]);
     const unsigned csEn = w < 3 ? cs(T.e[w + 1], M.e[w + 1], B.e[w + 1]) : cs(T.r, M.r, B.r);
     const unsigned ddEn = w < 3 ? dd(T.e[w + 1], B.e[w + 1]) : dd(T.r, B.r);
-    // odd pixels left of the even pair (4w-1, 4w+1); even pixels right of the odd pair (4w+2, 4w+4)
+    // odd pixels left of the even pair (4w - 1, 4w + 1); even pixels right of the odd pair (4w + 2, 4w + 4)
     const unsigned csOL = __byte_perm(csOp, csOc, 0x5432), ddOL = __byte_perm(ddOp, ddOc, 0x5432);
     const unsigned csER = __byte_perm(csEc, csEn, 0x5432), ddER = __byte_perm(ddEc, ddEn, 0x5432);
-    const int gxE = (int)(csOc - csOL);
-    const int gyE = (int)(ddOL + 2u * ddEc + ddOc - 0x04000400u);
-    const int gxO = (int)(csER - csEc);
-    const int gyO = (int)(ddEc + 2u * ddOc + ddER - 0x04000400u);
-    count_pair(gxE, gyE, M.e[w], 4 * w, lim, mclip, hs_sh, hg_adj);
-    count_pair(gxO, gyO, M.o[w], 4 * w + 1, lim, mclip, hs_sh, hg_adj);
+    const unsigned gxE = hsub2(csOc, csOL), gyE = hadd2(hfma2(ddEc, kHalfTwo, ddOL), ddOc);
+    const unsigned gxO = hsub2(csER, csEc), gyO = hadd2(hfma2(ddOc, kHalfTwo, ddEc), ddER);
+    float m0, m2, m1, m3;
+    m2_pair(gxE, gyE, m0, m2);
+    m2_pair(gxO, gyO, m1, m3);
+    const unsigned b0 = grad_bits_f(m0, mclipf), b1 = grad_bits_f(m1, mclipf);
+    const unsigned b2 = grad_bits_f(m2, mclipf), b3 = grad_bits_f(m3, mclipf);
+    if (!kEdge || 4 * w < cnt) red_sh(hg_adj + (b0 << 2));
+    if (!kEdge || 4 * w + 1 < cnt) red_sh(hg_adj + (b1 << 2));
+    if (!kEdge || 4 * w + 2 < cnt) red_sh(hg_adj + (b2 << 2));
+    if (!kEdge || 4 * w + 3 < cnt) red_sh(hg_adj + (b3 << 2));
     csOp = csOc; ddOp = ddOc; csEc = csEn; ddEc = ddEn;
   }
 }
 
-// One strip for one lane; returns whether a level above K - 1 was seen.  Rows yb .. yb + kBandH + 1
-// go through the warp's ring, kRing rows ahead of use.
+// Output rows [ya, yb) (yb <= H) of one strip column for one lane; rows ya - 1 .. yb pass through
+// the warp's ring, row r in slot (r - ya + 1) mod kSRing.  Returns whether a level above K - 1 was
+// seen.
 template <bool kEdge, bool kClamp>
-__device__ __forceinline__ bool hist_tile(const LaneTile& g, int yb, int mclip, unsigned kk, unsigned hs_sh,
-                                          unsigned hg_adj) {
-  constexpr int kRows = kBandH + 2;
+__device__ __forceinline__ bool roll_run(const SegLane& s, int ya, int yb, const unsigned char* wring,
+                                         unsigned wring_sh, unsigned hs_sh, unsigned hg_adj, float mclipf,
+                                         unsigned kk) {
   bool bad = false;
-  __syncwarp();  // (the previous tile's reads of the ring are done)
+  __syncwarp();  // (the previous run's reads of the ring are done)
 #pragma unroll
-  for (int r = 0; r < kRing; ++r) issue_row(g, r, yb + r, true);
-  cp_async_wait<kRing - 1>();
+  for (int k = 0; k < kSRing; ++k) roll_issue<kEdge>(s, wring_sh + k * kSSlot, ya - 1 + k, ya - 1 + k <= yb);
+  HRow R0, R1, R2;
+  cp_async_wait<kSRing - 1>();
   __syncwarp();
-  VRow v0 = build_row<kEdge, kClamp>(g, 0, yb, kk, bad);
+  roll_build<kEdge, kClamp>(R0, s, wring, false, hs_sh, kk, bad);
   __syncwarp();
-  issue_row(g, 0, yb + kRing, kRing < kRows);
-  cp_async_wait<kRing - 1>();
+  roll_issue<kEdge>(s, wring_sh, ya - 1 + kSRing, ya - 1 + kSRing <= yb);
+  cp_async_wait<kSRing - 1>();
   __syncwarp();
-  VRow v1 = build_row<kEdge, kClamp>(g, 1, yb + 1, kk, bad);
+  roll_build<kEdge, kClamp>(R1, s, wring + kSSlot, true, hs_sh, kk, bad);
   __syncwarp();
-  issue_row(g, 1, yb + kRing + 1, kRing + 1 < kRows);
-  const int full = kEdge ? min(g.cnt, 16) : 16;
-#pragma unroll
-  for (int j = 0; j < kBandH; ++j) {
-    cp_async_wait<kRing - 1>();
+  roll_issue<kEdge>(s, wring_sh + kSSlot, ya + kSRing, ya + kSRing <= yb);
+  int y = ya;
+  auto step = [&](const HRow& T, const HRow& M, HRow& B) {
+    const unsigned k = (unsigned)(y - ya + 2) & (kSRing - 1);  // slot of row y + 1
+    cp_async_wait<kSRing - 1>();
     __syncwarp();
-    const VRow v2 = build_row<kEdge, kClamp>(g, (j + 2) % kRing, yb + j + 2, kk, bad);
+    roll_build<kEdge, kClamp>(B, s, wring + k * kSSlot, y + 1 < yb, hs_sh, kk, bad);
     __syncwarp();
-    issue_row(g, (j + 2) % kRing, yb + j + 2 + kRing, j + 2 + kRing < kRows);
-    const int lim = kEdge ? (yb + j + 1 < g.H ? full : 0) : 16;
-    count_row(v0, v1, v2, lim, mclip, hs_sh, hg_adj);
-    v0 = v1;
-    v1 = v2;
+    roll_issue<kEdge>(s, wring_sh + k * kSSlot, y + 1 + kSRing, y + 1 + kSRing <= yb);
+    roll_sobel<kEdge>(T, M, B, s.cnt, mclipf, hg_adj);
+  };
+  for (;;) {
+    if (y >= yb) break;
+    step(R0, R1, R2);
+    ++y;
+    if (y >= yb) break;
+    step(R1, R2, R0);
+    ++y;
+    if (y >= yb) break;
+    step(R2, R0, R1);
+    ++y;
   }
+  cp_async_wait<0>();  // (the empty groups past the run's end)
   return bad;
 }
 
-// Tiles that cross the image's right or bottom edge, kept out of line so the interior path has
-// the register file to itself.
+// Runs of strip columns whose lanes do not all lie inside the image, kept out of line so the
+// interior path has the register file to itself.
 template <bool kClamp>
-__device__ __noinline__ bool hist_tile_edge(const LaneTile g, int yb, int mclip, unsigned kk, unsigned hs_sh,
-                                            unsigned hg_adj) {
-  return hist_tile<true, kClamp>(g, yb, mclip, kk, hs_sh, hg_adj);
+__device__ __noinline__ bool roll_run_edge(const SegLane s, int ya, int yb, const unsigned char* wring,
+                                           unsigned wring_sh, unsigned hs_sh, unsigned hg_adj, float mclipf,
+                                           unsigned kk) {
+  return roll_run<true, kClamp>(s, ya, yb, wring, wring_sh, hs_sh, hg_adj, mclipf, kk);
 }
 
 template <bool kClamp>
-__global__ void __launch_bounds__(kHT, 1) hist_u8r_kernel(const ImgTab tab, int total, int all_edge, int K,
+__global__ void __launch_bounds__(kHT, 1) hist_u8s_kernel(const ImgTab tab, int total, int all_edge, int K,
                                                          uint8_t* slots, size_t slot_bytes, SlotLayout lay,
                                                          unsigned* status) {
   pdl_wait();     // the previous kernel on the stream has finished
@@ -496,109 +525,101 @@ __global__ void __launch_bounds__(kHT, 1) hist_u8r_kernel(const ImgTab tab, int 
   const int n = tab.n;
   const int* __restrict__ unit_start = tab.units;  // (n > 1 only)
   extern __shared__ __align__(16) unsigned char hsmem[];
-  // per warp two copies (even and odd lanes, which see the most alike levels) of H_C(S), H_C(grad S)
-  auto hist = reinterpret_cast<unsigned (*)[2][2][kHBins]>(hsmem);
-  unsigned char* ring = hsmem + (size_t)kHW * 4 * kHBins * 4;
-  unsigned* nbr = reinterpret_cast<unsigned*>(ring + (size_t)kHW * kRing * kSlot);
-  __shared__ int next_tile;
+  // per warp two copies (even and odd lanes) of H_C(S), H_C(grad S), then the warps' rings
+  auto hist = reinterpret_cast<unsigned (*)[2][kHCopyWords]>(hsmem);
+  unsigned char* ring = hsmem + (size_t)kHW * 2 * kHCopyWords * 4;
   __shared__ int warp_img[kHW];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  unsigned* hw = &hist[warp][0][0][0];
-  for (int k = lane; k < 4 * kHBins; k += 32) hw[k] = 0u;
-  const int chunk = (total + gridDim.x - 1) / gridDim.x;
-  const int t0 = blockIdx.x * chunk, t1 = min(total, t0 + chunk);
-  if (tid == 0) next_tile = t0;
-  __syncthreads();
-
-  const unsigned hs_sh = (unsigned)__cvta_generic_to_shared(hist[warp][lane & 1][0]);
-  const unsigned hg_adj = (unsigned)__cvta_generic_to_shared(hist[warp][lane & 1][1]) - 0x2C000000u;  // - (0x4B000000 << 2)
-  const int mclip = K * K - K;
+  unsigned* hw = &hist[warp][0][0];
+  for (int k = lane; k < 2 * kHCopyWords; k += 32) hw[k] = 0u;
+  __syncwarp();
+  const unsigned hs_sh = (unsigned)__cvta_generic_to_shared(&hist[warp][lane & 1][0]);
+  const unsigned hg_adj = (unsigned)__cvta_generic_to_shared(&hist[warp][lane & 1][kHBins]) - 0x2C000000u;  // - (0x4B000000 << 2)
+  const float mclipf = (float)(K * K - K);
   const unsigned kk = 0x00010001u * (unsigned)(K - 1);
-  LaneTile g;
-  g.lx = lane;
-  g.slot0 = ring + (size_t)warp * kRing * kSlot;
-  g.ring = g.slot0 + 48 * lane;
-  g.nbr = nbr + warp * kRing * 32 + lane;
-  int cur = -1;
+  const unsigned char* wring = ring + (size_t)warp * kSRing * kSSlot;
+  const unsigned wring_sh = (unsigned)__cvta_generic_to_shared(wring);
+  // this warp's range of strip rows (kBandH per unit, units column-major within each image)
+  const long long Q = (long long)kBandH * total, NW = (long long)gridDim.x * kHW;
+  const long long gw = (long long)blockIdx.x * kHW + warp;
+  long long q = gw * Q / NW;
+  const long long q1 = (gw + 1) * Q / NW;
+  int cur = -1, img_u0 = 0, img_u1 = 0, nb = 1;
+  ImageDesc im{};
   bool bad = false;
   auto flush_warp = [&](int im_idx) {
     __syncwarp();
     unsigned* S = reinterpret_cast<unsigned*>(slots + (size_t)im_idx * slot_bytes + lay.S);
     unsigned* G = reinterpret_cast<unsigned*>(slots + (size_t)im_idx * slot_bytes + lay.G);
     for (int k = lane; k < K; k += 32) {
-      const unsigned sv = hist[warp][0][0][k] + hist[warp][1][0][k], gv = hist[warp][0][1][k] + hist[warp][1][1][k];
-      hist[warp][0][0][k] = hist[warp][1][0][k] = hist[warp][0][1][k] = hist[warp][1][1][k] = 0u;
+      const unsigned sv = hist[warp][0][k] + hist[warp][1][k], gv = hist[warp][0][kHBins + k] + hist[warp][1][kHBins + k];
+      hist[warp][0][k] = hist[warp][1][k] = hist[warp][0][kHBins + k] = hist[warp][1][kHBins + k] = 0u;
       if (sv) atomicAdd(S + k, sv);
       if (gv) atomicAdd(G + k, gv);
     }
     __syncwarp();
   };
-  // Units of one image: first its interior strips (row-major), then the edge strips (the right
-  // column, then the bottom band), so a warp runs one code path for long stretches: alternating
-  // paths thrash the instruction cache.  When edge strips are many (batches of small images),
-  // all strips take the edge path (all_edge).  A warp's units only grow, so the image is looked
-  // up again only when a unit passes the current image's end.
-  int img_start = 0, img_end = 0, nx = 0, nxi = 0, nyi = 0, n_int = 0, n_right = 0;
-  for (;;) {
-    int t = 0;
-    if (lane == 0) t = atomicAdd(&next_tile, 1);
-    t = __shfl_sync(0xffffffffu, t, 0);
-    if (t >= t1) break;
-    if (cur < 0 || t >= img_end) {
-      const int img = image_of_tile(unit_start, n, t);
+  SegLane s;
+  s.soff = 16u * (unsigned)(lane + 1);
+  s.roff = 16u + 48u * (unsigned)lane;
+  s.nbo = lane == 0 ? 12u : (unsigned)(16 + 3 * kStripW);
+  s.sel0 = lane == 0 ? 0x4441u : 0x4440u;
+  s.sel1 = lane == 0 ? 0x4442u : 0x4441u;
+  s.sel2 = lane == 0 ? 0x4443u : 0x4442u;
+  s.sxo = lane == 0 ? 0u : (unsigned)(16 + 3 * kStripW);
+  s.lane0 = lane == 0;
+  s.lane31 = lane == 31;
+  while (q < q1) {
+    const int u = (int)(q / kBandH);
+    if (cur < 0 || u >= img_u1) {  // a warp's strip rows only grow
+      const int img = n == 1 ? 0 : image_of_tile(unit_start, n, u);
       if (cur >= 0 && img != cur) flush_warp(cur);
       cur = img;
-      const ImageDesc im = tab.desc(img);
-      g.in = im.in;
-      g.pitch = im.in_pitch;
-      g.W = im.W;
-      g.H = im.H;
-      img_start = tab.unit0(img);
-      img_end = n == 1 ? total : tab.unit0(img + 1);
-      nx = (g.W + kStripW - 1) / kStripW;
-      nxi = g.W / kStripW;
-      nyi = g.H / kBandH;
-      n_int = nxi * nyi;
-      n_right = (nx - nxi) * nyi;
+      im = tab.desc(img);
+      img_u0 = tab.unit0(img);
+      img_u1 = n == 1 ? total : tab.unit0(img + 1);
+      nb = (im.H + kBandH - 1) / kBandH;
     }
-    const int lt = t - img_start;
-    int sx, sy;
-    if (lt < n_int) {
-      sy = lt / nxi;
-      sx = lt - sy * nxi;
-    } else if (lt - n_int < n_right) {
-      sx = nxi;
-      sy = lt - n_int;
-    } else {
-      sx = lt - n_int - n_right;
-      sy = nyi;
-    }
-    g.x0 = sx * kStripW;
-    const int y0 = sy * kBandH;
-    g.xc = g.x0 + 16 * g.lx;
-    g.cnt = g.W - g.xc;
-    const int yb = y0 - 1;
-    if (all_edge || lt >= n_int) bad |= hist_tile_edge<kClamp>(g, yb, mclip, kk, hs_sh, hg_adj);
-    else bad |= hist_tile<false, kClamp>(g, yb, mclip, kk, hs_sh, hg_adj);
+    const int sx = (u - img_u0) / nb;
+    const long long qc0 = (long long)kBandH * (img_u0 + (long long)sx * nb);  // the column's first strip row
+    const long long qe = min(q1, qc0 + (long long)kBandH * nb);
+    const int ya = (int)(q - qc0), yb = min((int)(qe - qc0), im.H);
+    q = qe;
+    if (ya >= yb) continue;
+    const int x0 = sx * kStripW;
+    s.in = im.in;
+    s.pitch = im.in_pitch;
+    s.H = im.H;
+    s.goff = 3 * x0 + 16 * lane;
+    s.rowbytes = 3 * im.W;
+    s.cnt = im.W - (x0 + 16 * lane);
+    const int rb = 3 * (im.W - x0 - kStripW);  // bytes right of the strip in a row
+    s.left_nb = x0 > 0;
+    s.right_nb = rb > 0;
+    s.xoff = lane == 0 ? 3 * x0 - 16 : 3 * (x0 + kStripW);
+    s.xbytes = lane == 0 ? (s.left_nb ? 16 : 0) : (lane == 1 ? min(max(rb, 0), 16) : 0);
+    s.use_nb = (s.lane0 && s.left_nb) || (s.lane31 && s.right_nb);
+    if (all_edge || x0 + kStripW > im.W)
+      bad |= roll_run_edge<kClamp>(s, ya, yb, wring, wring_sh, hs_sh, hg_adj, mclipf, kk);
+    else
+      bad |= roll_run<false, kClamp>(s, ya, yb, wring, wring_sh, hs_sh, hg_adj, mclipf, kk);
   }
   // the warps' last images: sum the warps that share an image, one global add per level
   if (lane == 0) warp_img[warp] = cur;
   __syncthreads();
-  {
-    for (int idx = tid; idx < 2 * kHBins; idx += kHT) {
-      const int which = idx / kHBins, k = idx % kHBins;
-      if (k >= K) continue;
-      for (int w = 0; w < kHW; ++w) {
-        const int im_idx = warp_img[w];
-        bool first = im_idx >= 0;
-        for (int u = 0; u < w && first; ++u) first = warp_img[u] != im_idx;
-        if (!first) continue;
-        unsigned s = 0;
-        for (int u = w; u < kHW; ++u)
-          if (warp_img[u] == im_idx) s += hist[u][0][which][k] + hist[u][1][which][k];
-        unsigned* dst = reinterpret_cast<unsigned*>(slots + (size_t)im_idx * slot_bytes + (which ? lay.G : lay.S));
-        if (s) atomicAdd(dst + k, s);
-      }
+  for (int idx = tid; idx < 2 * kHBins; idx += kHT) {
+    const int which = idx / kHBins, k = idx % kHBins;
+    if (k >= K) continue;
+    for (int w = 0; w < kHW; ++w) {
+      const int im_idx = warp_img[w];
+      bool first = im_idx >= 0;
+      for (int v = 0; v < w && first; ++v) first = warp_img[v] != im_idx;
+      if (!first) continue;
+      unsigned sum = 0;
+      for (int v = w; v < kHW; ++v)
+        if (warp_img[v] == im_idx) sum += hist[v][0][which * kHBins + k] + hist[v][1][which * kHBins + k];
+      unsigned* dst = reinterpret_cast<unsigned*>(slots + (size_t)im_idx * slot_bytes + (which ? lay.G : lay.S));
+      if (sum) atomicAdd(dst + k, sum);
     }
   }
   if (bad) atomicOr(status, kStRange);
@@ -868,7 +889,7 @@ __global__ void grad_level_probe_kernel(int form, int K, int m2_first, int n, ui
     const int m2 = m2_first + t;
     unsigned g;
     if (form == 0) {
-      g = strip_grad_bits(m2, mclip) - 0x4B000000u;
+      g = grad_bits_f((float)m2, (float)mclip) - 0x4B000000u;  // m2 < 2^24: exact in FP32
     } else if (form == 1) {
       g = grad_level(m2, K);
     } else {
@@ -902,13 +923,13 @@ cudaError_t launch_hist(const ImgTab& tab, int total_tiles, int total_units, int
     const dim3 grid(sms);
     const int all_edge = 8LL * interior_units < 7LL * total_units ? 1 : 0;  // more than 1/8 edge strips
     if (K < kHBins) {
-      cudaFuncSetAttribute(hist_u8r_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem);
-      return launch_kernel(hist_u8r_kernel<true>, grid, dim3(kHT), kHistSmem, st, pdl, tab, total_units, all_edge, K, slots,
-                           slot_bytes, lay, status);
+      cudaFuncSetAttribute(hist_u8s_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRollSmem);
+      return launch_kernel(hist_u8s_kernel<true>, grid, dim3(kHT), kRollSmem, st, pdl, tab, total_units, all_edge, K,
+                           slots, slot_bytes, lay, status);
     }
-    cudaFuncSetAttribute(hist_u8r_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHistSmem);
-    return launch_kernel(hist_u8r_kernel<false>, grid, dim3(kHT), kHistSmem, st, pdl, tab, total_units, all_edge, K, slots,
-                         slot_bytes, lay, status);
+    cudaFuncSetAttribute(hist_u8s_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRollSmem);
+    return launch_kernel(hist_u8s_kernel<false>, grid, dim3(kHT), kRollSmem, st, pdl, tab, total_units, all_edge, K,
+                         slots, slot_bytes, lay, status);
   }
   int grid = sms * ctas_per_sm;
   if (grid > total_tiles) grid = total_tiles;
