@@ -40,19 +40,22 @@ def parse():
     ap.add_argument("--width", type=int, default=7680)
     ap.add_argument("--height", type=int, default=4320)
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, per-size and CPU-baseline legs")
-    ap.add_argument("--streams", type=int, default=4, help="CUDA streams the timed steps go to, round-robin")
+    ap.add_argument("--streams", type=int, default=16, help="CUDA streams the timed steps go to, round-robin")
+    ap.add_argument("--partitions", type=int, default=1, help="16-SM solve partitions of single-image calls")
+    ap.add_argument("--partition-cluster", type=int, default=4,
+                    help="CTAs per solve of a partitioned call (each partition runs 16 / this many at once)")
     ap.add_argument("--serving-seconds", type=float, default=0.0,
                     help="long serving runs: seconds per rate (first 5 s left out of the statistics)")
     ap.add_argument("--serving-rates", default="800,1600", help="request rates of the long serving runs")
     return ap.parse_args()
 
 
-def workload_config(W, H, streams=1):
+def workload_config(W, H, streams=1, partitions=0, partition_cluster=16):
     return {"workload": f"plain single image {W}x{H} uint8 RGB, K=256, T=10 fixed iterations, gamma=2.2, "
                         f"alpha=beta=1e-3, FP64 solve; one histretinex_enhance call per step, steps round-robin on "
                         f"{streams} CUDA stream(s); 3 rotating input/output buffers (inputs larger than L2 in aggregate)",
             "image": f"{W}x{H}", "K": 256, "iterations": 10, "elem": "uint8", "l2": "rotating inputs > L2",
-            "streams": streams}
+            "streams": streams, "solve_partitions": partitions, "partition_cluster": partition_cluster}
 
 
 def make_images(W, H, rank=0):
@@ -181,7 +184,7 @@ def run_reference(a, rank, world):
     sample = f"rows 0-{rows - 1} of the {W}x{H} image ({rows * W / 1e6:.2f} MP) per step, single-threaded FP64 C oracle"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": el * 1000 / a.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(W, H, a.streams),
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(W, H, a.streams, a.partitions, a.partition_cluster),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -226,12 +229,14 @@ def batched_leg(torch, hr, local, precision, n_imgs=512, steps=10, warmup=3, see
     ms = e0.elapsed_time(e1) / steps
     byts = 3 * 3 * mp * 1e6  # read for the histograms, read + write for the apply
     arith = {hr.PREC_FP64: "FP64", hr.PREC_DF64: "double-float"}[precision]
-    # the same images, one histretinex_enhance call each, round-robin on 4 streams (3 solve partitions)
+    # the same images, one histretinex_enhance call each, round-robin on 16 streams (unpartitioned:
+    # the fastest single-call form for images of this size)
+    ns = 16
     single = hr.Context(hr.Params(precision=precision), device=local)
-    single.set_tuning(partitions=3)
-    sts = [torch.cuda.current_stream()] + [torch.cuda.Stream() for _ in range(3)]
+    single.set_tuning(partitions=0)
+    sts = [torch.cuda.current_stream()] + [torch.cuda.Stream() for _ in range(ns - 1)]
     for k in range(8):
-        single.enhance(ins[k], outs[k], stream=sts[k % 4])
+        single.enhance(ins[k], outs[k], stream=sts[k % ns])
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(sts[0])
@@ -240,7 +245,7 @@ def batched_leg(torch, hr, local, precision, n_imgs=512, steps=10, warmup=3, see
     reps = 3
     for _ in range(reps):
         for k in range(n_imgs):
-            single.enhance(ins[k], outs[k], stream=sts[k % 4])
+            single.enhance(ins[k], outs[k], stream=sts[k % ns])
     for st in sts[1:]:
         ev = torch.cuda.Event()
         ev.record(st)
@@ -255,8 +260,8 @@ def batched_leg(torch, hr, local, precision, n_imgs=512, steps=10, warmup=3, see
             "MP": mp, "ms_per_batch": ms, "MP_per_s": mp / (ms / 1e3), "tuning": tune,
             "gpu_launches_per_batch": (ctx.kernel_launches() - l0) / steps, "pipeline_GBps": byts / (ms / 1e3) / 1e9,
             "same_images_single_calls": {"ms": ms_single, "MP_per_s": mp / (ms_single / 1e3),
-                                         "how": "one histretinex_enhance per image, round-robin on 4 streams, "
-                                                "3 solve partitions"}}
+                                         "how": "one histretinex_enhance per image, round-robin on 16 streams, "
+                                                "unpartitioned"}}
 
 
 def precision_leg(torch, hr, local, n_imgs=1024, steps=2, warmup=1):
@@ -403,7 +408,7 @@ def serving_leg(torch, hr, local, big_img, seconds=5.0, rates=(400.0,), seed=5, 
     """Continuous batching under Poisson arrivals of mixed-size 8-bit requests (40 GB device budget,
     3 streams), at each rate in `rates` for `seconds` (statistics over the requests arriving after
     warm_s); then capacity: `capacity_requests` requests all queued at once, served by the same
-    server, against the same requests sent one by one through histretinex_enhance on 4 streams."""
+    server, against the same requests sent one by one through histretinex_enhance on 16 streams."""
     from paper_2510_21100_gb300 import serve, synth
     pool, weights = serving_pool(torch, synth, seed)
     pool.append(torch.from_numpy(big_img).pin_memory())
@@ -427,11 +432,11 @@ def serving_leg(torch, hr, local, big_img, seconds=5.0, rates=(400.0,), seed=5, 
         r.arrival = 0.0
     sc = srv.run(cap).summary()
     srv.close()
-    pl = serve.plain_throughput(cap, hr.Params(), streams=4, partitions=3, device=local)
+    pl = serve.plain_throughput(cap, hr.Params(), streams=16, partitions=0, device=local)
     out["capacity"] = {"requests": len(cap), "MP": sum(r.megapixels for r in cap),
                        "served_MP_per_s": sc["MP_per_s"], "served_p50_ms": sc["p50_ms"], "served_batches": sc["batches"],
-                       "plain_MP_per_s": pl["MP_per_s"], "plain": "one histretinex_enhance per request, 4 streams, "
-                       "3 solve partitions, host-to-device copy of each request included (as in the server)"}
+                       "plain_MP_per_s": pl["MP_per_s"], "plain": "one histretinex_enhance per request, 16 streams, "
+                       "unpartitioned, host-to-device copy of each request included (as in the server)"}
     return out
 
 
@@ -526,10 +531,12 @@ def main():
     dins = [torch.from_numpy(im).cuda() for im in imgs]
     douts = [torch.empty_like(d) for d in dins]
     ctx = hr.Context(hr.Params(), device=local)
+    ctx.set_tuning(partitions=a.partitions, partition_cluster=a.partition_cluster)
     # per-kernel durations: a second timed loop of the same workload on a context that records CUDA
     # events around each stage (events between the kernels keep them from overlapping, so the
-    # headline loop above runs without them)
+    # headline loop above runs without them), its solves on clusters of the headline's size
     sctx = hr.Context(hr.Params(stage_timing=True), device=local)
+    sctx.set_tuning(solve_cluster=a.partition_cluster if a.partitions > 0 else 16)
 
     uuid = None
     try:
@@ -564,12 +571,17 @@ def main():
     solve_flops = 2.0 * cells * (3 * dbg["iters"] + 1)
     h_ms, s_ms, a_ms = stage
     stages = {"hist": h_ms, "solve": s_ms, "apply": a_ms}
-    dom = max(stages, key=stages.get)
+    # the dominant kernel by SM time (duration x SMs it holds): the solve's cluster holds a few SMs
+    # while the pixel passes hold them all
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_time = {"hist": h_ms * n_sm, "solve": s_ms * (a.partition_cluster if a.partitions > 0 else 16),
+               "apply": a_ms * n_sm}
+    dom = max(sm_time, key=sm_time.get)
     # FP64 peak: 2 DFMA per SM per clock x 152 SMs x 2.07 GHz x 2 flops = 1259 GFLOP/s; a throughput
     # probe of dependent-free DFMA loops measured 1190-1200 on this GPU (no measured FP64 peak)
     fp64_peak = 1200.0
     # the strip kernel runs when the image has at least 2 strips (512 x 4 pixels) per warp of a full grid
-    hist_name = "hist_u8r_kernel" if -(-W // 512) * -(-H // 4) >= 2 * 16 * 152 else "hist_u8v_kernel"
+    hist_name = "hist_u8s_kernel" if -(-W // 512) * -(-H // 4) >= 2 * 8 * 152 else "hist_u8v_kernel"
     kern = {
         "hist": {"kernel": hist_name, "bound": "hbm", "achieved": hist_bytes / (h_ms / 1e3) / 1e9,
                  "peak": pk["hbm_gbs"], "unit": "GB/s", "peak_source": pk_src},
@@ -588,12 +600,15 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-        "data": "synthetic", "config": workload_config(W, H, a.streams), "gpu_launches": launches,
-        "stages_ms": stages,
+        "data": "synthetic", "config": workload_config(W, H, a.streams, a.partitions, a.partition_cluster),
+        "gpu_launches": launches,
+        "stages_ms": stages, "stage_sm_ms": sm_time, "dominant_by": "SM time (stage duration x SMs held)",
         "streams": a.streams,
         "partitions": {"solve_partitions": part_info[0], "pixel_sms": part_info[1],
-                       "note": "single-image calls: solves on 16-SM green-context partitions, pixel passes on "
-                               "the remaining SMs; steps on different streams overlap"},
+                       "partition_cluster": a.partition_cluster,
+                       "note": f"single-image calls: solves on 16-SM green-context partitions, each running "
+                               f"{16 // a.partition_cluster} {a.partition_cluster}-CTA solves at once, pixel passes "
+                               f"on the remaining SMs; steps on different streams overlap"},
         "single_stream": {"ms_per_step": ms_one / a.steps, "MP_per_s": mp / (ms_one / a.steps / 1e3)},
         "latency_ms": lat,
         "stage_loop": {"ms_per_step": ms_staged / a.steps,
@@ -635,21 +650,31 @@ def main():
             ims = make_images(w2, h2)
             di = [hr.to_device_aligned(im, f"cuda:{local}") for im in ims]
             do = [hr.aligned_empty(h2, w2, device=f"cuda:{local}") for _ in ims]
-            c2 = hr.Context(hr.Params(), device=local)
-            c2.set_tuning(partitions=3)  # smaller images: three 16-SM solve partitions (measured best below 8K)
+            st = max(100, a.steps // 2)
+            # single-image calls on a.streams streams: unpartitioned, and on 1 or 2 solve partitions
+            # of four 4-CTA solves each; the best of the three is the size's figure
+            tried = {}
+            for tn, tk in (("unpartitioned", dict(partitions=0)),
+                           ("1 partition, 4-CTA solves", dict(partitions=1, partition_cluster=4)),
+                           ("2 partitions, 4-CTA solves", dict(partitions=2, partition_cluster=4))):
+                c2 = hr.Context(hr.Params(), device=local)
+                c2.set_tuning(**tk)
+                mt, _, _ = timed_loop(c2, di, do, st, max(3, a.warmup // 2), None, torch, n_streams=a.streams)
+                tried[tn] = mt / st
+                if tn == "unpartitioned":
+                    m1, _, _ = timed_loop(c2, di, do, st, max(3, a.warmup // 2), None, torch)
+                c2.close()
+            best = min(tried, key=tried.get)
             c3 = hr.Context(hr.Params(stage_timing=True), device=local)
-            st = max(50, a.steps // 4)
-            mt, _, _ = timed_loop(c2, di, do, st, max(3, a.warmup // 2), None, torch, n_streams=a.streams)
-            m1, _, _ = timed_loop(c2, di, do, st, max(3, a.warmup // 2), None, torch)
             _, _, stg = timed_loop(c3, di, do, st, max(3, a.warmup // 2), None, torch, staged=True)
             c3.close()
-            ms2 = mt / st
+            ms2 = tried[best]
             rl = (2 * 3 * w2 * h2 + 3 * w2 * h2) / (pk["hbm_gbs"] * 1e9) * 1e3
             per[f"{w2}x{h2}"] = {"MP_per_s": w2 * h2 / 1e6 / (ms2 / 1000), "ms_per_image": ms2,
-                                 "streams": a.streams, "solve_partitions": 3, "single_stream_ms_per_image": m1 / st,
+                                 "streams": a.streams, "tuning": best,
+                                 "ms_per_image_by_tuning": tried, "single_stream_ms_per_image": m1 / st,
                                  "stages_ms": {"hist": stg[0], "solve": stg[1], "apply": stg[2]},
                                  "roofline_frac": rl / ms2}
-            c2.close()
         line["per_size"] = per
         line["batched"] = batched_leg(torch, hr, local, hr.PREC_DF64)
         line["batched_fp64"] = batched_leg(torch, hr, local, hr.PREC_FP64)

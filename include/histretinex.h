@@ -128,11 +128,16 @@ typedef struct hr_ctx hr_ctx;
  * other's pixel passes).  partitions: 0, or the number (1..4) of 16-SM partitions the GPU's SMs are
  * split into for the solves of single-image calls, the remaining SMs forming one partition for their
  * pixel passes (green contexts; default 2).  A call then runs its histogram and apply passes in the
- * pixel partition and its solve in the next solve partition, on the context's own streams, forked
- * from and joined back into the caller's stream; calls on different caller streams overlap (one
- * image's solve beside other images' pixel passes), with results bit-identical to partitions = 0.
- * Single-image calls then use a ring of four workspace slots, each call the next.  Calls under
- * stream capture or with stage timing, and devices whose SMs cannot be split so, run unpartitioned. */
+ * pixel partition and its solve in a solve partition, on the context's own streams, forked from and
+ * joined back into the caller's stream; calls on different caller streams overlap (one image's
+ * solve beside other images' pixel passes).  partition_cluster: CTAs per cluster of those solves
+ * (1, 2, 4, 8 or 16; default 16); each solve partition runs 16 / partition_cluster of them at once
+ * (smaller clusters take longer per image but use the SMs better: for a stream of 7680x4320 images
+ * on many caller streams, partitions = 1 with partition_cluster = 4 gives the highest throughput).  A partitioned call's results are
+ * bit-identical to the same call unpartitioned with solve_cluster = partition_cluster.
+ * Single-image calls use a ring of workspace slots, each call the next (16 slots for workspaces of
+ * up to 16 MB, else 4).  Calls under stream capture or with stage timing, and devices whose SMs
+ * cannot be split so, run unpartitioned. */
 typedef struct {
   int hist_ctas_per_sm;
   int apply_ctas_per_sm;
@@ -141,6 +146,7 @@ typedef struct {
   int pdl;
   int groups;
   int partitions;
+  int partition_cluster;
 } hr_tuning;
 
 /* Fills *p with the defaults: K = 256, alpha = beta = 1e-3, gamma = 2.2 (Sec. III.C),
@@ -158,7 +164,7 @@ hr_status histretinex_create(hr_ctx** out, const hr_params* p, int device);
  * in_pitch, out_pitch: row strides in bytes; elem_bytes: 1 or 2.
  * Asynchronous on `stream`: the call reads its input after the stream's earlier work and its
  * output is complete when the stream reaches the work queued after it.  Calls on different
- * streams may overlap on the device: each takes the next of the context's four single-image
+ * streams may overlap on the device: each takes the next of the context's single-image
  * workspace slots and its device work waits for that slot's previous call, so such calls need no
  * ordering by the caller (with SM partitions, hr_tuning.partitions > 0, one call's solve then runs
  * beside other calls' pixel passes).  Under stream capture a call uses the context's first batch

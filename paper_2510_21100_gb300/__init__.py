@@ -54,6 +54,7 @@ class hr_tuning(ctypes.Structure):
         ("pdl", ctypes.c_int),
         ("groups", ctypes.c_int),
         ("partitions", ctypes.c_int),
+        ("partition_cluster", ctypes.c_int),
     ]
 
 
@@ -383,7 +384,8 @@ class Context:
         """Changes launch shapes (histretinex_set_tuning; fields as in hr_tuning): hist_ctas_per_sm,
         apply_ctas_per_sm (1..32), solve_cluster (1, 2, 4, 8, 16), use_graph (0/1), pdl (mask 0..7 of
         the kernels launched as programmatic dependent launches), groups (1/2 for large batches),
-        partitions (0..4 solve partitions of 16 SMs for single-image calls).
+        partitions (0..4 solve partitions of 16 SMs for single-image calls), partition_cluster (1, 2, 4,
+        8, 16: CTAs per solve of a partitioned call; each partition runs 16 / partition_cluster at once).
         Fields not given keep their current values; invalid values raise and change nothing."""
         cur = self.tuning()
         cur.update(kw)

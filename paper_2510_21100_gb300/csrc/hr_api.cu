@@ -50,24 +50,26 @@ struct hr_ctx {
   int ev_next = 0;
   double stage_ms[3] = {0, 0, 0};
   int stage_calls = 0;
-  hr_tuning tune{8, 16, 16, 1, 5, 2, 2};
+  hr_tuning tune{8, 16, 16, 1, 5, 2, 2, 16};
   // leading slots whose H_C(S) and H_C(grad S) are known to be zero (the solve clears them after
   // use unless the intermediates are kept for histretinex_get_debug)
   int hist_clean = 0;
   // captured batch pipeline and the geometry it was captured for
   cudaGraphExec_t graph = nullptr;
   int g_n = 0, g_total = 0, g_eb = 0, g_fast_in = 0, g_fast_out = 0, g_zero = 0, g_groups = 0, g_launches = 0;
-  hr_tuning g_tune{0, 0, 0, 0, 0, 0, 0};
+  hr_tuning g_tune{0, 0, 0, 0, 0, 0, 0, 0};
   int last_groups = 0;  // groups of the uploaded tables
   // single-image calls on SM partitions: a ring of workspace slots, each known clean or not
-  static constexpr int kRingSlots = 4;
+  static constexpr int kRingMax = 16;
   hr::Partitions* part = nullptr;
   int part_parts = 0;               // partitions the current Partitions object was made with
+  int part_sper = 0;                // and its solve streams per partition
   bool part_unavailable = false;    // the split failed on this device: run unpartitioned
   uint8_t* d_ring = nullptr;
-  bool ring_clean[kRingSlots] = {};
-  cudaEvent_t ring_free[kRingSlots] = {};  // recorded on the caller's stream after the slot's last call
-  bool ring_pending[kRingSlots] = {};
+  int ring_n = 0;                   // slots of the ring: 16 for workspaces up to 16 MB, else 4
+  bool ring_clean[kRingMax] = {};
+  cudaEvent_t ring_free[kRingMax] = {};  // recorded on the caller's stream after the slot's last call
+  bool ring_pending[kRingMax] = {};
   int ring_next = 0;
   const uint8_t* last_base = nullptr;  // slot 0 of the last call's images (debug reads)
 };
@@ -362,17 +364,25 @@ void note_hist_state(hr_ctx* c, int n, bool ok) {
 // Single-image calls take the slots of a ring in turn.  A call first makes its stream wait until
 // the slot's previous call (on whatever stream) is done, and marks the slot's release on its own
 // stream after its last kernel, so calls on different streams may overlap on the device.
-hr_status ring_acquire(hr_ctx* c, cudaStream_t st, int* r) {
-  if (!c->d_ring) {
-    HR_CUDA(cudaMalloc(&c->d_ring, c->lay.bytes * (size_t)hr_ctx::kRingSlots));
-    for (int i = 0; i < hr_ctx::kRingSlots; ++i) {
-      c->ring_clean[i] = false;
-      c->ring_pending[i] = false;
-      if (!c->ring_free[i]) HR_CUDA(cudaEventCreateWithFlags(&c->ring_free[i], cudaEventDisableTiming));
-    }
+hr_status ring_alloc(hr_ctx* c) {
+  if (c->d_ring) return HR_OK;
+  const int n = c->lay.bytes <= ((size_t)16 << 20) ? hr_ctx::kRingMax : 4;
+  HR_CUDA(cudaMalloc(&c->d_ring, c->lay.bytes * (size_t)n));
+  for (int i = 0; i < n; ++i) {
+    c->ring_clean[i] = false;
+    c->ring_pending[i] = false;
+    if (!c->ring_free[i]) HR_CUDA(cudaEventCreateWithFlags(&c->ring_free[i], cudaEventDisableTiming));
   }
+  c->ring_n = n;
+  c->ring_next = 0;
+  return HR_OK;
+}
+
+hr_status ring_acquire(hr_ctx* c, cudaStream_t st, int* r) {
+  const hr_status s = ring_alloc(c);
+  if (s != HR_OK) return s;
   *r = c->ring_next;
-  c->ring_next = (*r + 1) % hr_ctx::kRingSlots;
+  c->ring_next = (*r + 1) % c->ring_n;
   if (c->ring_pending[*r]) HR_CUDA(cudaStreamWaitEvent(st, c->ring_free[*r], 0));
   return HR_OK;
 }
@@ -422,15 +432,20 @@ hr_status run_partitioned(hr_ctx* c, const ImageDesc& d, int elem_bytes, bool fa
                           cudaStream_t st, bool* done) {
   *done = false;
   if (c->part_unavailable) return HR_OK;
-  if (c->part && c->part_parts != c->tune.partitions) {
+  // solves of partition_cluster CTAs, 16 / partition_cluster of them at once in each 16-SM partition
+  const int sper = 16 / c->tune.partition_cluster;
+  if (c->part && (c->part_parts != c->tune.partitions || c->part_sper != sper)) {
     hr::partitions_destroy(c->part);  // (synchronises the partitions' streams)
     c->part = nullptr;
   }
   if (!c->part) {
-    const hr_status ps = hr::partitions_create(c->device, c->tune.partitions, hr_ctx::kRingSlots, &c->part);
+    hr_status ps = ring_alloc(c);
+    if (ps != HR_OK) return ps;
+    ps = hr::partitions_create(c->device, c->tune.partitions, sper, c->ring_n, &c->part);
     if (ps == HR_ERR_UNSUPPORTED) { c->part_unavailable = true; return HR_OK; }
     if (ps != HR_OK) return ps;
     c->part_parts = c->tune.partitions;
+    c->part_sper = sper;
   }
   int r = 0;
   hr_status rs = ring_acquire(c, st, &r);
@@ -458,7 +473,7 @@ hr_status run_partitioned(hr_ctx* c, const ImageDesc& d, int elem_bytes, bool fa
     return hr::launch_hist(g.tab, g.total, g.units, g.interior, elem_bytes, K, g.slots, c->lay.bytes, c->lay,
                            c->d_status, sms, c->tune.hist_ctas_per_sm, s, fast_in, false, forward, c->M);
   };
-  auto solve = [&](cudaStream_t s) { return hr::launch_solve(a, 1, solve_ctas(c, 1, false), s, false); };
+  auto solve = [&](cudaStream_t s) { return hr::launch_solve(a, 1, c->tune.partition_cluster, s, false); };
   auto apply = [&](cudaStream_t s) {
     return hr::launch_apply(g.tab, g.total, elem_bytes, K, g.slots, c->lay.bytes, c->lay, c->d_status, sms,
                             c->tune.apply_ctas_per_sm, s, fast_out, false, c->M);
@@ -906,7 +921,7 @@ hr_status histretinex_destroy(hr_ctx* c) {
   if (c->desc_done) cudaEventSynchronize(c->desc_done);
   hr::partitions_destroy(c->part);
   cudaFree(c->d_ring);
-  for (int i = 0; i < hr_ctx::kRingSlots; ++i)
+  for (int i = 0; i < hr_ctx::kRingMax; ++i)
     if (c->ring_free[i]) cudaEventDestroy(c->ring_free[i]);
   cudaFree(c->d_slots);
   cudaFree(c->d_jstart1);
@@ -971,6 +986,8 @@ hr_status histretinex_set_tuning(hr_ctx* c, const hr_tuning* t) {
   if (t->pdl < 0 || t->pdl > 7) return HR_ERR_INVALID_ARG;
   if (t->groups != 1 && t->groups != 2) return HR_ERR_INVALID_ARG;
   if (t->partitions < 0 || t->partitions > 4) return HR_ERR_INVALID_ARG;
+  if (t->partition_cluster < 1 || t->partition_cluster > 16 || (t->partition_cluster & (t->partition_cluster - 1)))
+    return HR_ERR_INVALID_ARG;
   c->tune = *t;
   return HR_OK;
 }

@@ -152,14 +152,14 @@ cudaError_t launch_grad_level_probe(int form, int K, int m2_first, int n, uint16
 size_t solve_smem_bytes(int K, int vec_in_smem, int list_in_smem, size_t fsize);
 
 // SM partitions for overlapping single-image calls (green contexts): `parts` partitions of 16 SMs
-// for solves and one of the remaining SMs for the pixel passes; `ring` pixel streams, one per
-// workspace slot.  partitions_run forks one call from the caller's stream st: hist on the slot's
-// pixel stream, solve on the next solve partition, apply back on the pixel stream, then st waits
-// for it.  Each StageFn enqueues its stage on the stream it is given (the partition's context is
+// for solves, each with `sper` solve streams, and one of the remaining SMs for the pixel passes;
+// `ring` pixel streams, one per workspace slot.  partitions_run forks one call from the caller's
+// stream st: hist on the slot's pixel stream, solve on the next solve stream (partitions in turn),
+// apply back on the pixel stream, then st waits for it.  Each StageFn enqueues its stage on the stream it is given (the partition's context is
 // current while it runs).
 using StageFn = std::function<cudaError_t(cudaStream_t)>;
 struct Partitions;
-hr_status partitions_create(int device, int parts, int ring, Partitions** out);
+hr_status partitions_create(int device, int parts, int sper, int ring, Partitions** out);
 void partitions_destroy(Partitions* P);
 int partitions_pixel_sms(const Partitions* P);
 cudaError_t partitions_run(Partitions* P, int slot, cudaStream_t st, const StageFn& hist, const StageFn& solve,
