@@ -28,7 +28,7 @@ UNIT = "MP/s"
 # DRAM bytes (read + write) per launch of each kernel at 7680x4320, K = 256, from one ncu capture
 # of the current kernels (profiles/pipeline_7680x4320_launches.md); the apply's writes still in L2
 # when the kernel ends are not counted there.
-PROFILED_DRAM_BYTES = {"hist_u8r_kernel": 105_511_680, "solve_kernel<double>": 219_136, "apply_u8v_kernel": 147_895_808}
+PROFILED_DRAM_BYTES = {"hist_u8s_kernel": 104_349_952, "solve_kernel<double>": 260_864, "apply_u8v_kernel": 147_757_312}
 
 
 def parse():

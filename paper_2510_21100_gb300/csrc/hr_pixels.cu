@@ -810,7 +810,9 @@ __global__ void __launch_bounds__(kThreads) hist_u8v_kernel(const ImgTab tab, in
   if (range_bad) atomicOr(status, kStRange);
 }
 
-__global__ void __launch_bounds__(kThreads) apply_u8v_kernel(const ImgTab tab, int total, int K,
+// kAll: K = 256, every 8-bit value is a level (no clamp, no range check).
+template <bool kAll>
+__global__ void __launch_bounds__(kThreads, 8) apply_u8v_kernel(const ImgTab tab, int total, int K,
                                                              const uint8_t* slots, size_t slot_bytes, SlotLayout lay,
                                                              unsigned* status) {
   pdl_wait();     // the previous kernel on the stream has finished
@@ -825,11 +827,13 @@ __global__ void __launch_bounds__(kThreads) apply_u8v_kernel(const ImgTab tab, i
   const int chunk = (total + gridDim.x - 1) / gridDim.x;
   const int t0 = blockIdx.x * chunk, t1 = min(total, t0 + chunk);
   const unsigned vmax = (unsigned)(K - 1);
-  int cur = -1;
   bool range_bad = false;
+  // a CTA's tiles are consecutive: the image and the tile's column and row advance incrementally
+  int img = -1, img_t1 = 0, tiles_x = 1, tx = 0, ty = 0;
+  ImageDesc im{};
   for (int t = t0; t < t1; ++t) {
-    const int img = image_of_tile(tile_start, n, t);
-    if (img != cur) {
+    if (t >= img_t1) {
+      img = img < 0 ? image_of_tile(tile_start, n, t) : img + 1;
       __syncthreads();
       const unsigned short* gl = reinterpret_cast<const unsigned short*>(slots + (size_t)img * slot_bytes + lay.lut);
       for (int k = tid; k < 256; k += kThreads) {
@@ -837,13 +841,19 @@ __global__ void __launch_bounds__(kThreads) apply_u8v_kernel(const ImgTab tab, i
         fb[k] = k == 0 ? make_uint2(0u, vp << 18) : make_uint2(((vp << 18) + (unsigned)k - 1u) / (unsigned)k, 1u << 17);
       }
       __syncthreads();
-      cur = img;
+      im = tab.desc(img);
+      img_t1 = n == 1 ? total : tab.tile0(img + 1);
+      tiles_x = (im.W + kTileW - 1) / kTileW;
+      const int lt = t - tab.tile0(img);
+      ty = lt / tiles_x;
+      tx = lt - ty * tiles_x;
     }
-    const ImageDesc im = tab.desc(img);
-    const int lt = t - tab.tile0(img);
-    const int tiles_x = (im.W + kTileW - 1) / kTileW;
-    const int x = (lt % tiles_x) * kTileW + 16 * (tid & 7);
-    const int y = (lt / tiles_x) * kTileH + (tid >> 3);
+    const int x = tx * kTileW + 16 * (tid & 7);
+    const int y = ty * kTileH + (tid >> 3);
+    if (++tx == tiles_x) {
+      tx = 0;
+      ++ty;
+    }
     if (y >= im.H || x >= im.W) continue;
     const unsigned char* src = im.in + (long long)y * im.in_pitch + 3LL * x;
     unsigned char* dst = im.out + (long long)y * im.out_pitch + 3LL * x;
@@ -859,12 +869,19 @@ __global__ void __launch_bounds__(kThreads) apply_u8v_kernel(const ImgTab tab, i
         unsigned ch[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) ch[q] = __byte_perm(w[(3 * p + q) >> 2], 0u, 0x4440 + ((3 * p + q) & 3));
-        unsigned V = max(max(ch[0], ch[1]), ch[2]);
-        range_bad |= V > vmax;
-        V = min(V, vmax);
+        unsigned V = __vimax3_u32(ch[0], ch[1], ch[2]);
+        if (!kAll) {
+          range_bad |= V > vmax;
+          V = min(V, vmax);
+        }
         const uint2 f = fb[V];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) o[(3 * p + q) >> 2] |= ((ch[q] * f.x + f.y) >> 18) << (8 * ((3 * p + q) & 3));
+        for (int q = 0; q < 3; ++q) {
+          // byte j of the output word: ((c F + B) >> 18) << 8 j, as one shift and a mask (c F + B < 2^26)
+          const unsigned t = ch[q] * f.x + f.y;
+          const int j = (3 * p + q) & 3;
+          o[(3 * p + q) >> 2] |= (j < 3 ? t >> (18 - 8 * j) : t << (8 * j - 18)) & (0xffu << (8 * j));
+        }
       }
       uint4* d4 = reinterpret_cast<uint4*>(dst);
       d4[0] = make_uint4(o[0], o[1], o[2], o[3]);
@@ -966,9 +983,13 @@ cudaError_t launch_apply(const ImgTab& tab, int total_tiles, int elem_bytes, int
   const int nt = elem_bytes == 1 ? M : K;
   const size_t smem = (size_t)((nt * 2 + 15) & ~15) + (size_t)nt * sizeof(float);
   const int grid = max(1, min(sms * ctas_per_sm, total_tiles));
-  if (elem_bytes == 1 && fast)
-    return launch_kernel(apply_u8v_kernel, dim3(grid), dim3(kThreads), 0, st, pdl, tab, total_tiles, K, slots,
+  if (elem_bytes == 1 && fast) {
+    if (K == 256)
+      return launch_kernel(apply_u8v_kernel<true>, dim3(grid), dim3(kThreads), 0, st, pdl, tab, total_tiles, K, slots,
+                           slot_bytes, lay, status);
+    return launch_kernel(apply_u8v_kernel<false>, dim3(grid), dim3(kThreads), 0, st, pdl, tab, total_tiles, K, slots,
                          slot_bytes, lay, status);
+  }
   if (elem_bytes == 1)
     return launch_kernel(apply_kernel<uint8_t>, dim3(grid), dim3(kThreads), smem, st, pdl, tab, total_tiles, K, slots,
                          slot_bytes, lay, status, shift, M);
