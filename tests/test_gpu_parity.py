@@ -155,9 +155,9 @@ def test_batch_equals_single_images(hr):
 
 
 def test_batch_of_large_images_takes_both_strip_paths(hr):
-    """Two large images in one batch (few edge strips: each image's interior strips on the interior
-    path, its edge strips on the edge path): histograms, LUT and pixels as each image gets alone
-    (there on the staged tiles, 4096 strips being below the strip kernel's threshold)."""
+    """Two large images in one batch (few edge strips: each image's full strip columns on the
+    interior path, the second image's partial last column on the edge path): histograms, LUT and
+    pixels as each image gets alone in a single call."""
     import torch
     from gpu_util import assert_close
     ctx, po = ctx_for(hr)
@@ -216,9 +216,10 @@ def test_batch_result_independent_of_batch_composition(hr):
 
 
 def test_large_batch_takes_strip_histograms(hr):
-    """A batch with enough 512 x 4 strips for the strip histogram kernel, which takes each image's
-    interior strips first and then its right column and bottom band: every image gets the
-    histograms, LUT and pixels it gets alone, and a few are checked against the oracle."""
+    """A batch with enough 512 x 4 strips for the rolling strip histogram kernel, whose warps take
+    equal runs of strip rows column by column, across image boundaries (interior and partial right
+    columns on their two code paths): every image gets the histograms, LUT and pixels it gets alone,
+    and a few are checked against the oracle."""
     import torch
     from gpu_util import assert_close
     ctx, po = ctx_for(hr)
@@ -265,9 +266,9 @@ def _strip_pad(W):
 
 
 def test_large_ragged_image(hr):
-    """A single image large enough for the strip histogram kernel (one warp per 512 x 4 strip),
-    with a partial last strip (7001 = 13 * 512 + 345: a lane holding 9 pixels) and a partial last
-    band (4001 = 1000 * 4 + 1)."""
+    """A single image large enough for the rolling strip histogram kernel (512-pixel strip columns
+    dealt out in runs of rows), with a partial last column (7001 = 13 * 512 + 345: a lane holding 9
+    pixels) and a partial last band (4001 = 1000 * 4 + 1)."""
     ctx, po = ctx_for(hr)
     img = synth.low_light_image(7001, 4001, seed=synth.seed_for(1, 7))
     out, dbg = run_gpu(ctx, img, pad_elems=_strip_pad(7001))
