@@ -477,10 +477,110 @@ __device__ void class_totals(const ClassPlan& P, const unsigned* csz, const unsi
   }
 }
 
+// ---- Run sums (the FP32 form for large K, one CTA per image) -------------------------------------
+// The cells of class k in row i are the support columns of one run, [posL[js(i, k)], posL[js(i, k+1)]),
+// and row i meets the classes from index(i, jmin) to index(i, jmax) (jmin, jmax: the first and last
+// support column).  A row sum over cells of (class weight) x (column weight) is then a sum over the
+// row's runs of (class weight) x (the run's column-weight sum), a difference of two prefix sums of the
+// column weights.  The class map is symmetric in i and j, so column sums are the same over row runs,
+// and class k meets the contiguous rows whose class span covers it, so class totals sum run sums over
+// those rows.  Prefix sums are double-float pairs: a difference loses nothing to cancellation (its
+// error is a few units of the difference's last place plus 2^-48 of the prefix).  Runs are about a
+// third of the cells at K = 4096, and no cell list is built.
+
+__device__ __forceinline__ df64 shfl_up_df(df64 v, int o) {
+  return df64(__shfl_up_sync(FULL, v.hi, o), __shfl_up_sync(FULL, v.lo, o));
+}
+
+// pre[p] = x(0) + ... + x(p - 1) for p in [0, n] as double-float (hi, lo) pairs; red holds NW values.
+template <class X>
+__device__ void prefix_df(int n, X x, float2* pre, df64* red) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int per = (n + NT - 1) / NT;
+  const int b0 = min(n, (int)threadIdx.x * per), b1 = min(n, b0 + per);
+  df64 s(0.f, 0.f);
+  for (int b = b0; b < b1; ++b) s += df64(x(b), 0.f);
+  df64 inc = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    const df64 y = shfl_up_df(inc, o);
+    if (l >= o) inc = inc + y;
+  }
+  df64 ex = shfl_up_df(inc, 1);
+  if (l == 0) ex = df64(0.f, 0.f);
+  __syncthreads();  // (the previous use of red is over)
+  if (l == 31) red[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    df64 t = l < NW ? red[l] : df64(0.f, 0.f);
+    for (int o = 1; o < 32; o <<= 1) {
+      const df64 y = shfl_up_df(t, o);
+      if (l >= o) t = t + y;
+    }
+    if (l < NW) red[l] = t;
+  }
+  __syncthreads();
+  df64 run = w > 0 ? red[w - 1] + ex : ex;
+  for (int b = b0; b < b1; ++b) {
+    pre[b] = make_float2(run.hi, run.lo);
+    run += df64(x(b), 0.f);
+  }
+  if ((b0 < b1 && b1 == n) || (n == 0 && threadIdx.x == 0)) pre[n] = make_float2(run.hi, run.lo);
+  __syncthreads();
+}
+
+// pre[p1] - pre[p0] (p1 >= p0) as a float.
+__device__ __forceinline__ float run_sum(const float2* pre, int p0, int p1) {
+  const float2 u = pre[p1], v = pre[p0];
+  return __fadd_rn(__fsub_rn(u.x, v.x), __fsub_rn(u.y, v.y));
+}
+
+// The runs of classes [kA, kB] of line i (row i of the class map, or column i: the map is symmetric),
+// by a whole warp, lanes over 31 classes at a time: f(k, s) is called by the lane of class k with
+// s = pre[pos[js(i, k + 1)]] - pre[pos[js(i, k)]] (each lane's upper boundary comes from the next lane).
+// The boundary js(i, k) = ceil(t / d), t = (2k - 1)(K - 1), d = 2i, is kept with its excess
+// e = q d - t in [0, d) and advanced 31 classes at a time (t grows by 62 (K - 1)) by integer steps:
+// one division per lane and one per line, none per run.  Line 0 holds one class, 0, over everything.
+template <class Fn>
+__device__ __forceinline__ void line_runs(int i, int kA, int kB, int K, const uint16_t* pos, const float2* pre, Fn f) {
+  const int lane = threadIdx.x & 31;
+  if (i == 0) {
+    if (lane == 0 && kA == 0) f(0, run_sum(pre, pos[0], pos[K]));
+    return;
+  }
+  const int km1 = K - 1, d = 2 * i;
+  // quotients from a float estimate made exact by remainder corrections: dt < 2^18 is exact in FP32,
+  // so dt / d is within 0.02 of the estimate (one step each way); |t| < 2^26 rounds by up to 2 and
+  // t / d < 2^17, so ceil(t / d) is within two of the estimate's ceiling (two steps each way)
+  const float rd = __frcp_rn((float)d);
+  const int dt = 62 * km1;
+  int dq = __float2int_rz(__fmul_rn((float)dt, rd));
+  dq += (dt - dq * d >= d) - (dt - dq * d < 0);
+  const int dr = dt - dq * d;
+  const int t = (2 * (kA + lane) - 1) * km1;
+  int q = __float2int_ru(__fmul_rn((float)t, rd));  // ceil(t / d), then e = q d - t in [0, d)
+  int e = q * d - t;
+  if (e < 0) { ++q; e += d; }
+  if (e < 0) { ++q; e += d; }
+  if (e >= d) { --q; e -= d; }
+  if (e >= d) { --q; e -= d; }
+#pragma unroll 2
+  for (int k0 = kA; k0 <= kB; k0 += 31) {
+    const int k = k0 + lane;
+    const int p = pos[min(max(q, 0), K)];
+    const float2 u = pre[p];
+    const int pn = __shfl_down_sync(FULL, p, 1);
+    const float hn = __shfl_down_sync(FULL, u.x, 1), ln = __shfl_down_sync(FULL, u.y, 1);
+    if (lane < 31 && k <= kB && pn > p) f(k, __fadd_rn(__fsub_rn(hn, u.x), __fsub_rn(ln, u.y)));
+    const int x = dr - e;
+    if (x > 0) { q += dq + 1; e = d - x; } else { q += dq; e = -x; }
+  }
+}
+
 template <typename F>
 __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ F conv[2][NW];
+  __shared__ df64 dred[NW];  // (prefix sums of the run form)
   const cg::cluster_group cl = cg::this_cluster();
   pdl_wait();     // the histogram pass before it on the stream has finished
   pdl_trigger();  // the apply pass may be scheduled (it waits for this kernel)
@@ -538,6 +638,12 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   F* Lu = vec + 5 * K;   // Eq. 12 before Eq. 14
   F* q = vec + 6 * K;    // S_k / P_k (level-indexed)
   F* Sd = vec + 7 * K;   // S as F (level-indexed)
+  // The run form (FP32, one CTA, the closed-form class map, K > 1024: the cell lists would not fit
+  // shared memory) replaces the class plan and its lists; its double-float prefix sums and the
+  // level -> row-position table posR take the plan's arrays csz, cst, pst (10 (K + 1) <= 12 K bytes).
+  const bool runs = std::is_same<F, float>::value && C == 1 && !A.cmap && !A.printed && K > 1024;
+  float2* pre = reinterpret_cast<float2*>(csz);
+  uint16_t* posR = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned char*>(csz) + (size_t)(K + 1) * sizeof(float2));
 
   // ---- supports and N (every CTA) -------------------------------------------------------------
   const int per = iceil_div(K, NT);
@@ -554,6 +660,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   const unsigned nRu = (unsigned)(tot64 & 0xffffu), nLu = (unsigned)((tot64 >> 16) & 0xffffu);
   const unsigned Nu = (unsigned)(tot64 >> 32);
   for (int k = k0; k < k1; ++k) {
+    if (runs) posR[k] = (uint16_t)offR;
     if (G[k] > 0u) RI[offR++] = (uint16_t)k;
     posL[k] = (uint16_t)offL;
     if (S[k] > 0u) LJ[offL++] = (uint16_t)k;
@@ -561,6 +668,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     q[k] = 0.0;
   }
   if (tid == 0) posL[K] = (uint16_t)nLu;
+  if (tid == 0 && runs) posR[K] = (uint16_t)nRu;
   __syncthreads();
   const int nR = (int)nRu, nL = (int)nLu;
   const F N = (F)Nu;
@@ -580,12 +688,14 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     for (int a = tid; a < nR; a += NT) mg[a] = RI[a] ? ~0ull / (2ull * RI[a]) + 1ull : 0ull;
     __syncthreads();
   }
-  const ClassPlan PP = plan_classes(cl, nR, nL, RI, posL, JsIndex{K, RI, mg, A.jstart0}, [&](int c) { return (int)LJ[c]; }, csz, cst,
-                                    pst, ob, ured, rank, C);
+  ClassPlan PP{};
+  if (!runs)
+    PP = plan_classes(cl, nR, nL, RI, posL, JsIndex{K, RI, mg, A.jstart0}, [&](int c) { return (int)LJ[c]; }, csz, cst,
+                      pst, ob, ured, rank, C);
   stamp();
   // owner CTA of every class of the plan: rank r holds the classes whose first cell lies in
   // [cells r / C, cells (r + 1) / C) (rank 0 also those below, the last rank those above)
-  {
+  if (!runs) {
     __shared__ unsigned rank_lo[kMaxCluster];
     if (tid < C) rank_lo[tid] = (unsigned)(((unsigned long long)PP.cells * tid) / C);
     __syncthreads();
@@ -651,11 +761,51 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
       }  // (the second reciprocal needs the first: a chain)
     }
     // row weights of the Eq. 13 sums: L^2 (stationary point of Eq. 10), 1 (Eq. 13 as printed)
-    for (int b = tid; b < nL; b += NT) { const F x = L0[b]; L2c[b] = A.printed ? (F)1.0 : x * x; }
+    if (!runs)
+      for (int b = tid; b < nL; b += NT) { const F x = L0[b]; L2c[b] = A.printed ? (F)1.0 : x * x; }
     if (it == 1) stamp();
-    class_totals<F>(PP, csz, pst, R0, L0, [&](int c, F Pu) { RRc[c] = Pu; });  // (R'R is free until Eq. 13)
+    if constexpr (std::is_same<F, float>::value) {
+      if (runs) {
+        // class totals from run sums, row by row: each warp adds R_i x (run sum of L) of its own rows,
+        // in order, into its partial totals, for CW = K / 4 classes at a time (the partials take the
+        // four vectors free at this point, 4 warps x CW in each); the partials are summed in warp order
+        for (int c = tid; c < nL; c += NT) RRc[c] = 0.f;  // (classes above every cell's class stay 0)
+        prefix_df(nL, [&](int b) { return L0[b]; }, pre, dred);
+        const int jmin = LJ[0], jmax = LJ[nL - 1];
+        const int CW = K / 4;
+        float* bufs[4] = {R1, L1, L2c, q};  // (free until the new q is formed)
+        float* part = bufs[warp >> 2] + (warp & 3) * CW;
+        const int rA = (int)((long long)nR * warp / NW), rB = (int)((long long)nR * (warp + 1) / NW);
+        const int kall = class_index(RI[nR - 1], jmax, km1, cdiv);  // the largest class of any cell
+        for (int c0 = 0; c0 <= kall; c0 += CW) {
+          for (int k = lane; k < CW; k += 32) part[k] = 0.f;
+          __syncwarp();
+          for (int a = rA; a < rB; ++a) {
+            const int i = RI[a];
+            const int kA = max(class_index(i, jmin, km1, cdiv), c0);
+            const int kB = min(class_index(i, jmax, km1, cdiv), c0 + CW - 1);
+            if (kA > kB) continue;
+            const float r = R0[a];
+            line_runs(i, kA, kB, K, posL, pre, [&](int k, float sm) { part[k - c0] = fmaf(r, sm, part[k - c0]); });
+            __syncwarp();  // (the next row's classes may fall to other lanes)
+          }
+          __syncthreads();
+          for (int k = c0 + tid; k < min(c0 + CW, K); k += NT) {
+            if (Sd[k] > 0.f) {
+              float P = 0.f;
+              for (int w = 0; w < NW; ++w) P += (bufs[w >> 2] + (w & 3) * CW)[k - c0];
+              RRc[posL[k]] = P;
+            }
+          }
+          __syncthreads();
+        }
+        for (int k = tid; k < K; k += NT) q[k] = 0.f;  // (the partials used it; classes with S_k = 0 keep q = 0)
+      }
+    }
+    if (!runs) class_totals<F>(PP, csz, pst, R0, L0, [&](int c, F Pu) { RRc[c] = Pu; });  // (R'R is free until Eq. 13)
     __syncthreads();
-    for (int c = PP.cA + tid; c < PP.cB; c += NT) {  // q of all own classes together (scal[3] is set)
+    const int qc0 = runs ? 0 : PP.cA, qc1 = runs ? nL : PP.cB;
+    for (int c = qc0 + tid; c < qc1; c += NT) {  // q of all own classes together (scal[3] is set)
       const int k = LJ[c];
       const F P = RRc[c] * (scR * scal[3]);
       // q_k = S_k / P_k; as printed the weight K_ij = R_i L_j / P_k divides, so q_k = S_k P_k
@@ -672,8 +822,27 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     // Eq. 13 for the own rows: lane groups of GA over the illumination bins.
     {
       const F rdR = scal[0], sl2 = A.printed ? (F)1.0 : scL * scL;
+      if constexpr (std::is_same<F, float>::value) {
+        if (runs) {  // a warp per row over its runs, column weights L^2 through their prefix sums
+          prefix_df(nL, [&](int b) { const float x = L0[b]; return x * x; }, pre, dred);
+          const int jmin = LJ[0], jmax = LJ[nL - 1];
+          for (int a = warp; a < nR; a += NW) {
+            const int i = RI[a];
+            float acc = 0.f;
+            line_runs(i, class_index(i, jmin, km1, cdiv), class_index(i, jmax, km1, cdiv), K, posL, pre,
+                      [&](int k, float sm) { acc = fmaf(q[k], sm, acc); });
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+            if (lane == 0) {
+              const F r = scR * R0[a];
+              const F ru = fmaF(r * invN, acc * sl2, beta * (F)G[i]) * rdR;
+              R1[a] = ru;
+              RRc[a] = ru * r;
+            }
+          }
+        }
+      }
       const int gi = lane / GA, gl = lane % GA, rpw = 32 / GA;
-      for (int a0 = aA + warp * rpw; a0 < aB; a0 += NW * rpw) {
+      for (int a0 = aA + warp * rpw; a0 < (runs ? aA : aB); a0 += NW * rpw) {
         const int a = a0 + gi;
         F acc = 0.0;
         if (a < aB) {
@@ -721,8 +890,22 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     }
     {
       F* Bs = L2c;  // column sums (L^2 is not needed again in this iteration)
+      if constexpr (std::is_same<F, float>::value) {
+        if (runs) {  // a warp per column over its runs through the rows, row weights R' R by prefix sums
+          prefix_df(nR, [&](int a) { return RRc[a]; }, pre, dred);
+          const int imin = RI[0], imax = RI[nR - 1];
+          for (int b = warp; b < nL; b += NW) {
+            const int j = LJ[b];
+            float acc = 0.f;
+            line_runs(j, class_index(imin, j, km1, cdiv), class_index(imax, j, km1, cdiv), K, posR, pre,
+                      [&](int k, float sm) { acc = fmaf(q[k], sm, acc); });
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+            if (lane == 0) Bs[b] = acc;
+          }
+        }
+      }
       const int gi = lane / GB, gl = lane % GB, cpw = 32 / GB;
-      for (int b0 = bA + warp * cpw; b0 < bB; b0 += NW * cpw) {
+      for (int b0 = bA + warp * cpw; b0 < (runs ? bA : bB); b0 += NW * cpw) {
         const int b = b0 + gi;
         F acc = 0.0;
         if (b < bB) {
