@@ -535,11 +535,12 @@ __device__ __forceinline__ float run_sum(const float2* pre, int p0, int p1) {
 }
 
 // The runs of classes [kA, kB] of line i (row i of the class map, or column i: the map is symmetric),
-// by a whole warp, lanes over 31 classes at a time: f(k, s) is called by the lane of class k with
-// s = pre[pos[js(i, k + 1)]] - pre[pos[js(i, k)]] (each lane's upper boundary comes from the next lane).
-// The boundary js(i, k) = ceil(t / d), t = (2k - 1)(K - 1), d = 2i, is kept with its excess
-// e = q d - t in [0, d) and advanced 31 classes at a time (t grows by 62 (K - 1)) by integer steps:
-// one division per lane and one per line, none per run.  Line 0 holds one class, 0, over everything.
+// by a whole warp: lane l takes the l-th of 32 contiguous blocks of the classes and calls f(k, s) for
+// each of its classes k, s = pre[pos[js(i, k + 1)]] - pre[pos[js(i, k)]].  The boundary
+// js(i, k) = ceil(t / d), t = (2k - 1)(K - 1), d = 2i, is kept with its excess e = q d - t in [0, d)
+// and advanced one class at a time (t grows by 2 (K - 1)) by integer steps: one division per lane and
+// one per line, none per run, and a lane's loads for successive classes depend only on those steps.
+// Line 0 holds one class, 0, over everything.
 template <class Fn>
 __device__ __forceinline__ void line_runs(int i, int kA, int kB, int K, const uint16_t* pos, const float2* pre, Fn f) {
   const int lane = threadIdx.x & 31;
@@ -547,17 +548,57 @@ __device__ __forceinline__ void line_runs(int i, int kA, int kB, int K, const ui
     if (lane == 0 && kA == 0) f(0, run_sum(pre, pos[0], pos[K]));
     return;
   }
+  const int per = (kB - kA + 32) >> 5;
+  const int kS = kA + lane * per, kE = min(kB, kS + per - 1);
+  if (kS > kE) return;
   const int km1 = K - 1, d = 2 * i;
-  // quotients from a float estimate made exact by remainder corrections: dt < 2^18 is exact in FP32,
-  // so dt / d is within 0.02 of the estimate (one step each way); |t| < 2^26 rounds by up to 2 and
-  // t / d < 2^17, so ceil(t / d) is within two of the estimate's ceiling (two steps each way)
+  // quotients from a float estimate made exact by remainder corrections: dt < 2^13 and |t| < 2^26
+  // (t / d < 2^17): the estimates are within 0.02 and within two of the exact values
+  const float rd = __frcp_rn((float)d);
+  const int dt = 2 * km1;
+  int dq = __float2int_rz(__fmul_rn((float)dt, rd));
+  dq += (dt - dq * d >= d) - (dt - dq * d < 0);
+  const int dr = dt - dq * d;
+  const int t = (2 * kS - 1) * km1;
+  int q = __float2int_ru(__fmul_rn((float)t, rd));  // ceil(t / d), then e = q d - t in [0, d)
+  int e = q * d - t;
+  if (e < 0) { ++q; e += d; }
+  if (e < 0) { ++q; e += d; }
+  if (e >= d) { --q; e -= d; }
+  if (e >= d) { --q; e -= d; }
+  int p = pos[min(max(q, 0), K)];
+  float2 u = pre[p];
+#pragma unroll 4
+  for (int k = kS; k <= kE; ++k) {
+    const int x = dr - e;
+    if (x > 0) { q += dq + 1; e = d - x; } else { q += dq; e = -x; }
+    const int pn = pos[min(q, K)];
+    const float2 un = pre[pn];
+    if (pn > p) f(k, __fadd_rn(__fsub_rn(un.x, u.x), __fsub_rn(un.y, u.y)));
+    p = pn;
+    u = un;
+  }
+}
+
+// The same runs with lanes over 31 consecutive classes at a time (each lane's upper boundary from
+// the next lane), for callers that scatter into per-class arrays: the lanes of one step touch
+// consecutive entries (no shared-memory bank conflicts).  The boundary advances 31 classes per step.
+template <class Fn>
+__device__ __forceinline__ void line_runs_il(int i, int kA, int kB, int K, const uint16_t* pos, const float2* pre, Fn f) {
+  const int lane = threadIdx.x & 31;
+  if (i == 0) {
+    if (lane == 0 && kA == 0) f(0, run_sum(pre, pos[0], pos[K]));
+    return;
+  }
+  const int km1 = K - 1, d = 2 * i;
+  // (estimates made exact as in line_runs: dt < 2^18 exact in FP32, |t| < 2^26)
   const float rd = __frcp_rn((float)d);
   const int dt = 62 * km1;
   int dq = __float2int_rz(__fmul_rn((float)dt, rd));
   dq += (dt - dq * d >= d) - (dt - dq * d < 0);
   const int dr = dt - dq * d;
   const int t = (2 * (kA + lane) - 1) * km1;
-  int q = __float2int_ru(__fmul_rn((float)t, rd));  // ceil(t / d), then e = q d - t in [0, d)
+  int q = __float2int_ru(__fmul_rn((float)t, rd));
   int e = q * d - t;
   if (e < 0) { ++q; e += d; }
   if (e < 0) { ++q; e += d; }
@@ -573,6 +614,31 @@ __device__ __forceinline__ void line_runs(int i, int kA, int kB, int K, const ui
     if (lane < 31 && k <= kB && pn > p) f(k, __fadd_rn(__fsub_rn(hn, u.x), __fsub_rn(ln, u.y)));
     const int x = dr - e;
     if (x > 0) { q += dq + 1; e = d - x; } else { q += dq; e = -x; }
+  }
+}
+
+// Classes of index_1 met by row i, from its first (jmin) and last (jmax) support column: k0 + 1 =
+// #{k < K : js1(i, k) <= jmin}, likewise k1 for jmax, capped at i (index_1 never exceeds i: a_j <= 1).
+// js1 grows with k and js1(i, 0) = 0, so each count is found by a 32-ary search: the lanes probe 32
+// boundaries stride apart, a ballot counts those within the column, the search continues from the
+// last of them with a stride 32 times smaller (three rounds at K = 4096, one for K <= 32), both
+// counts side by side.  The whole warp calls it.
+__device__ __forceinline__ void index1_span(const uint16_t* jr, int K, int i, int jmin, int jmax, int& k0, int& k1) {
+  const int lane = threadIdx.x & 31;
+  int s0 = 0, s1 = 0, stride = 1;
+  while (stride * 32 < K) stride *= 32;
+  for (;;) {
+    const int ka = s0 + lane * stride, kb = s1 + lane * stride;
+    const int m0 = __popc(__ballot_sync(FULL, ka < K && (int)jr[ka] <= jmin));  // >= 1: the probe at s0
+    const int m1 = __popc(__ballot_sync(FULL, kb < K && (int)jr[kb] <= jmax));
+    if (stride == 1) {
+      k0 = s0 + m0 - 1;
+      k1 = min(s1 + m1 - 1, i);
+      return;
+    }
+    s0 += (m0 - 1) * stride;
+    s1 += (m1 - 1) * stride;
+    stride /= 32;
   }
 }
 
@@ -773,8 +839,11 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         prefix_df(nL, [&](int b) { return L0[b]; }, pre, dred);
         const int jmin = LJ[0], jmax = LJ[nL - 1];
         const int CW = K / 4;
-        float* bufs[4] = {R1, L1, L2c, q};  // (free until the new q is formed)
-        float* part = bufs[warp >> 2] + (warp & 3) * CW;
+        auto bufs = [&](int w) {  // (free until the new q is formed)
+          const int b = w >> 2;
+          return (b == 0 ? R1 : b == 1 ? L1 : b == 2 ? L2c : q) + (w & 3) * CW;
+        };
+        float* part = bufs(warp);
         const int rA = (int)((long long)nR * warp / NW), rB = (int)((long long)nR * (warp + 1) / NW);
         const int kall = class_index(RI[nR - 1], jmax, km1, cdiv);  // the largest class of any cell
         for (int c0 = 0; c0 <= kall; c0 += CW) {
@@ -786,14 +855,15 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
             const int kB = min(class_index(i, jmax, km1, cdiv), c0 + CW - 1);
             if (kA > kB) continue;
             const float r = R0[a];
-            line_runs(i, kA, kB, K, posL, pre, [&](int k, float sm) { part[k - c0] = fmaf(r, sm, part[k - c0]); });
+            line_runs_il(i, kA, kB, K, posL, pre, [&](int k, float sm) { part[k - c0] = fmaf(r, sm, part[k - c0]); });
             __syncwarp();  // (the next row's classes may fall to other lanes)
           }
           __syncthreads();
           for (int k = c0 + tid; k < min(c0 + CW, K); k += NT) {
             if (Sd[k] > 0.f) {
               float P = 0.f;
-              for (int w = 0; w < NW; ++w) P += (bufs[w >> 2] + (w & 3) * CW)[k - c0];
+#pragma unroll
+              for (int w = 0; w < NW; ++w) P += bufs(w)[k - c0];
               RRc[posL[k]] = P;
             }
           }
@@ -977,6 +1047,79 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
   Lc = L0;
 
   // ---- Eq. 17-20: enhanced histogram through the index_1 class map -----------------------------
+  F* T = L2c;      // level-indexed enhanced histogram (rank 0)
+  F sl = (F)0.0;   // the final L scale
+  bool target_done = false;
+  if constexpr (std::is_same<F, float>::value) {
+    if (runs) {
+      // run form: T_k = (1/N) sum_i R_i (run sum of L), the run sums from prefix sums of L, each
+      // warp adding R_i x run sum of its own rows, in order, into partial targets for CW = K / 4
+      // classes at a time (in the four vectors free until the LUT), summed in warp order; the
+      // rows' class spans go where S as a float was (not needed again)
+      uint16_t* rs0 = reinterpret_cast<uint16_t*>(Sd);
+      uint16_t* rs1 = rs0 + K;
+      prefix_df(nL, [&](int b) { return Lc[b]; }, pre, dred);
+      sl = scal[4];
+      const int jmin = LJ[0], jmax = LJ[nL - 1];
+      for (int a = warp; a < nR; a += NW) {
+        const int i = RI[a];
+        int k0, k1;
+        index1_span(A.jstart1 + (size_t)i * (K + 1), K, i, jmin, jmax, k0, k1);
+        if (lane == 0) { rs0[a] = (uint16_t)k0; rs1[a] = (uint16_t)k1; }
+      }
+      __syncthreads();
+      const int CW = K / 4;
+      auto bufs = [&](int w) {
+        const int b = w >> 2;
+        return (b == 0 ? R1 : b == 1 ? L1 : b == 2 ? q : RRc) + (w & 3) * CW;
+      };
+      float* part = bufs(warp);
+      const int rA = (int)((long long)nR * warp / NW), rB = (int)((long long)nR * (warp + 1) / NW);
+      const int kall = RI[nR - 1];  // (index_1 never exceeds i)
+      int c0 = 0;
+      for (; c0 <= kall; c0 += CW) {
+        for (int k = lane; k < CW; k += 32) part[k] = 0.f;
+        __syncwarp();
+        for (int a = rA; a < rB; ++a) {
+          const int kA = max((int)rs0[a], c0), kB = min((int)rs1[a], c0 + CW - 1);
+          if (kA > kB) continue;
+          const uint16_t* jr = A.jstart1 + (size_t)RI[a] * (K + 1);  // js1(i, k), k <= K (entry K holds K)
+          const float r = Rc[a];
+          // lane l: the l-th of 32 contiguous blocks of the classes, so its table loads for successive
+          // classes are independent of each other (measured faster here than lanes over consecutive
+          // classes, whose shared-memory updates avoid bank conflicts but whose loads wait in turn)
+          const int per = (kB - kA + 32) >> 5;
+          const int kS = kA + lane * per, kE = min(kB, kS + per - 1);
+          if (kS <= kE) {
+            int p = posL[jr[kS]];
+            float2 u = pre[p];
+#pragma unroll 4
+            for (int k = kS; k <= kE; ++k) {
+              const int pn = posL[jr[k + 1]];
+              const float2 un = pre[pn];
+              if (pn > p) part[k - c0] = fmaf(r, __fadd_rn(__fsub_rn(un.x, u.x), __fsub_rn(un.y, u.y)), part[k - c0]);
+              p = pn;
+              u = un;
+            }
+          }
+          __syncwarp();  // (the next row's classes may fall to other lanes)
+        }
+        __syncthreads();
+        for (int k = c0 + tid; k < min(c0 + CW, K); k += NT) {
+          float sum = 0.f;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) sum += bufs(w)[k - c0];
+          T[k] = sum;
+        }
+        __syncthreads();
+      }
+      const F tscale = invN * (scR * sl);  // the count matrix carries 1/N (Eq. 6); R and L their scales
+      for (int k = tid; k < K; k += NT) T[k] = k < c0 ? T[k] * tscale : (F)0.0;
+      __syncthreads();
+      target_done = true;
+    }
+  }
+  if (!target_done) {
   // The cells of class k in row i (Eq. 19) are the support columns of [js1(i, k), js1(i, k+1)),
   // so T_k = (1/N) sum_i R_i (sum of L over that run).  Row i meets the classes [k0, k1] of its
   // first and last support column (index_1 grows with j, and is at most i).  Row pass (own rows):
@@ -1011,26 +1154,8 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     for (int a = aA + warp; a < aB; a += NW) {  // own rows, a warp each
       const int i = RI[a];
       const uint16_t* jr = A.jstart1 + (size_t)i * (K + 1);  // js1(i, k), k <= K (entry K holds K)
-      // classes of the first and last support column: k0 + 1 = #{k < K : js1(i, k) <= jmin}, likewise
-      // k1 for jmax.  js1 grows with k and js1(i, 0) = 0, so each count is found by a 32-ary search:
-      // the lanes probe 32 boundaries stride apart, a ballot counts those within the column, the
-      // search continues from the last of them with a stride 32 times smaller (three rounds at
-      // K = 4096, one for K <= 32), both counts side by side.
-      int c0 = 0, c1 = 0;
-      {
-        int s0 = 0, s1 = 0, stride = 1;
-        while (stride * 32 < K) stride *= 32;
-        for (;;) {
-          const int ka = s0 + lane * stride, kb = s1 + lane * stride;
-          const int m0 = __popc(__ballot_sync(FULL, ka < K && (int)jr[ka] <= jmin));  // >= 1: the probe at s0
-          const int m1 = __popc(__ballot_sync(FULL, kb < K && (int)jr[kb] <= jmax));
-          if (stride == 1) { c0 = s0 + m0; c1 = s1 + m1; break; }
-          s0 += (m0 - 1) * stride;
-          s1 += (m1 - 1) * stride;
-          stride /= 32;
-        }
-      }
-      const int k0 = c0 - 1, k1 = min(c1 - 1, i);  // (index_1 never exceeds i: a_j <= 1)
+      int k0, k1;
+      index1_span(jr, K, i, jmin, jmax, k0, k1);
       if (lane == 0) { rk0[a] = (unsigned)k0; rk1[a] = (unsigned)k1; }
       const F r = Rc[a];
       F* out = wacc ? wacc + (size_t)warp * K : seg_of(a);
@@ -1073,9 +1198,8 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     cluster_wait();
     return;
   }
-  const F sl = scal[4];
+  sl = scal[4];
   const F tscale = invN * (scR * sl);  // the count matrix carries 1/N (Eq. 6); R and L their scales
-  F* T = L2c;  // level-indexed target (rank 0, in place of its own partial)
   for (int k = tid; k < K; k += NT) {
     F v[kMaxCluster];
 #pragma unroll
@@ -1086,6 +1210,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     T[k] = sum * tscale;
   }
   __syncthreads();
+  }
   cluster_arrive_relaxed();  // the other CTAs may leave (this CTA waits for that phase at its end)
   stamp();
 
