@@ -548,7 +548,9 @@ __device__ __forceinline__ void line_runs(int i, int kA, int kB, int K, const ui
     if (lane == 0 && kA == 0) f(0, run_sum(pre, pos[0], pos[K]));
     return;
   }
-  const int per = (kB - kA + 32) >> 5;
+  // (an odd block length: the lanes' accesses to per-class arrays, per entries apart, fall in
+  // distinct shared-memory banks)
+  const int per = ((kB - kA + 32) >> 5) | 1;
   const int kS = kA + lane * per, kE = min(kB, kS + per - 1);
   if (kS > kE) return;
   const int km1 = K - 1, d = 2 * i;
@@ -832,8 +834,8 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
     if (it == 1) stamp();
     if constexpr (std::is_same<F, float>::value) {
       if (runs) {
-        // class totals from run sums, row by row: each warp adds R_i x (run sum of L) of its own rows,
-        // in order, into its partial totals, for CW = K / 4 classes at a time (the partials take the
+        // class totals from run sums, row by row: each warp adds R_i x (run sum of L) of its rows (every
+        // NW-th), in order, into its partial totals, for CW = K / 4 classes at a time (the partials take the
         // four vectors free at this point, 4 warps x CW in each); the partials are summed in warp order
         for (int c = tid; c < nL; c += NT) RRc[c] = 0.f;  // (classes above every cell's class stay 0)
         prefix_df(nL, [&](int b) { return L0[b]; }, pre, dred);
@@ -844,12 +846,11 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
           return (b == 0 ? R1 : b == 1 ? L1 : b == 2 ? L2c : q) + (w & 3) * CW;
         };
         float* part = bufs(warp);
-        const int rA = (int)((long long)nR * warp / NW), rB = (int)((long long)nR * (warp + 1) / NW);
         const int kall = class_index(RI[nR - 1], jmax, km1, cdiv);  // the largest class of any cell
         for (int c0 = 0; c0 <= kall; c0 += CW) {
           for (int k = lane; k < CW; k += 32) part[k] = 0.f;
           __syncwarp();
-          for (int a = rA; a < rB; ++a) {
+          for (int a = warp; a < nR; a += NW) {  // (rows strided over the warps: their lengths grow with a)
             const int i = RI[a];
             const int kA = max(class_index(i, jmin, km1, cdiv), c0);
             const int kB = min(class_index(i, jmax, km1, cdiv), c0 + CW - 1);
@@ -1074,13 +1075,12 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         return (b == 0 ? R1 : b == 1 ? L1 : b == 2 ? q : RRc) + (w & 3) * CW;
       };
       float* part = bufs(warp);
-      const int rA = (int)((long long)nR * warp / NW), rB = (int)((long long)nR * (warp + 1) / NW);
       const int kall = RI[nR - 1];  // (index_1 never exceeds i)
       int c0 = 0;
       for (; c0 <= kall; c0 += CW) {
         for (int k = lane; k < CW; k += 32) part[k] = 0.f;
         __syncwarp();
-        for (int a = rA; a < rB; ++a) {
+        for (int a = warp; a < nR; a += NW) {  // (rows strided over the warps: their lengths grow with a)
           const int kA = max((int)rs0[a], c0), kB = min((int)rs1[a], c0 + CW - 1);
           if (kA > kB) continue;
           const uint16_t* jr = A.jstart1 + (size_t)RI[a] * (K + 1);  // js1(i, k), k <= K (entry K holds K)
@@ -1088,7 +1088,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
           // lane l: the l-th of 32 contiguous blocks of the classes, so its table loads for successive
           // classes are independent of each other (measured faster here than lanes over consecutive
           // classes, whose shared-memory updates avoid bank conflicts but whose loads wait in turn)
-          const int per = (kB - kA + 32) >> 5;
+          const int per = ((kB - kA + 32) >> 5) | 1;  // (odd: the partials' banks differ)
           const int kS = kA + lane * per, kE = min(kB, kS + per - 1);
           if (kS <= kE) {
             int p = posL[jr[kS]];
