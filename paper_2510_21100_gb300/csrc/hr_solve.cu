@@ -478,15 +478,15 @@ __device__ void class_totals(const ClassPlan& P, const unsigned* csz, const unsi
 }
 
 // ---- Run sums (the FP32 form for large K, one CTA per image) -------------------------------------
-// The cells of class k in row i are the support columns of one run, [posL[js(i, k)], posL[js(i, k+1)]),
+// The cells of class k in row i are the support columns with levels in [js(i, k), js(i, k+1)) (a run),
 // and row i meets the classes from index(i, jmin) to index(i, jmax) (jmin, jmax: the first and last
 // support column).  A row sum over cells of (class weight) x (column weight) is then a sum over the
 // row's runs of (class weight) x (the run's column-weight sum), a difference of two prefix sums of the
-// column weights.  The class map is symmetric in i and j, so column sums are the same over row runs,
-// and class k meets the contiguous rows whose class span covers it, so class totals sum run sums over
-// those rows.  Prefix sums are double-float pairs: a difference loses nothing to cancellation (its
-// error is a few units of the difference's last place plus 2^-48 of the prefix).  Runs are about a
-// third of the cells at K = 4096, and no cell list is built.
+// column weights, indexed by level (zero weight at the levels outside the support, so an empty run
+// adds exactly zero).  The class map is symmetric in i and j, so column sums are the same over row
+// runs, and class totals scatter each row's run sums by class.  Prefix sums are double-float pairs: a
+// difference loses nothing to cancellation (its error is a few units of the difference's last place
+// plus 2^-48 of the prefix).  Runs are about a third of the cells at K = 4096, and no cell list is built.
 
 __device__ __forceinline__ df64 shfl_up_df(df64 v, int o) {
   return df64(__shfl_up_sync(FULL, v.hi, o), __shfl_up_sync(FULL, v.lo, o));
@@ -536,16 +536,16 @@ __device__ __forceinline__ float run_sum(const float2* pre, int p0, int p1) {
 
 // The runs of classes [kA, kB] of line i (row i of the class map, or column i: the map is symmetric),
 // by a whole warp: lane l takes the l-th of 32 contiguous blocks of the classes and calls f(k, s) for
-// each of its classes k, s = pre[pos[js(i, k + 1)]] - pre[pos[js(i, k)]].  The boundary
+// each of its classes k, s = pre[js(i, k + 1)] - pre[js(i, k)] (pre indexed by level).  The boundary
 // js(i, k) = ceil(t / d), t = (2k - 1)(K - 1), d = 2i, is kept with its excess e = q d - t in [0, d)
 // and advanced one class at a time (t grows by 2 (K - 1)) by integer steps: one division per lane and
 // one per line, none per run, and a lane's loads for successive classes depend only on those steps.
 // Line 0 holds one class, 0, over everything.
 template <class Fn>
-__device__ __forceinline__ void line_runs(int i, int kA, int kB, int K, const uint16_t* pos, const float2* pre, Fn f) {
+__device__ __forceinline__ void line_runs(int i, int kA, int kB, int K, const float2* pre, Fn f) {
   const int lane = threadIdx.x & 31;
   if (i == 0) {
-    if (lane == 0 && kA == 0) f(0, run_sum(pre, pos[0], pos[K]));
+    if (lane == 0 && kA == 0) f(0, run_sum(pre, 0, K));
     return;
   }
   // (an odd block length: the lanes' accesses to per-class arrays, per entries apart, fall in
@@ -568,16 +568,13 @@ __device__ __forceinline__ void line_runs(int i, int kA, int kB, int K, const ui
   if (e < 0) { ++q; e += d; }
   if (e >= d) { --q; e -= d; }
   if (e >= d) { --q; e -= d; }
-  int p = pos[min(max(q, 0), K)];
-  float2 u = pre[p];
+  float2 u = pre[min(max(q, 0), K)];
 #pragma unroll 4
   for (int k = kS; k <= kE; ++k) {
     const int x = dr - e;
     if (x > 0) { q += dq + 1; e = d - x; } else { q += dq; e = -x; }
-    const int pn = pos[min(q, K)];
-    const float2 un = pre[pn];
-    if (pn > p) f(k, __fadd_rn(__fsub_rn(un.x, u.x), __fsub_rn(un.y, u.y)));
-    p = pn;
+    const float2 un = pre[min(q, K)];
+    f(k, __fadd_rn(__fsub_rn(un.x, u.x), __fsub_rn(un.y, u.y)));  // (an empty run adds exactly 0)
     u = un;
   }
 }
@@ -586,10 +583,10 @@ __device__ __forceinline__ void line_runs(int i, int kA, int kB, int K, const ui
 // the next lane), for callers that scatter into per-class arrays: the lanes of one step touch
 // consecutive entries (no shared-memory bank conflicts).  The boundary advances 31 classes per step.
 template <class Fn>
-__device__ __forceinline__ void line_runs_il(int i, int kA, int kB, int K, const uint16_t* pos, const float2* pre, Fn f) {
+__device__ __forceinline__ void line_runs_il(int i, int kA, int kB, int K, const float2* pre, Fn f) {
   const int lane = threadIdx.x & 31;
   if (i == 0) {
-    if (lane == 0 && kA == 0) f(0, run_sum(pre, pos[0], pos[K]));
+    if (lane == 0 && kA == 0) f(0, run_sum(pre, 0, K));
     return;
   }
   const int km1 = K - 1, d = 2 * i;
@@ -609,11 +606,9 @@ __device__ __forceinline__ void line_runs_il(int i, int kA, int kB, int K, const
 #pragma unroll 2
   for (int k0 = kA; k0 <= kB; k0 += 31) {
     const int k = k0 + lane;
-    const int p = pos[min(max(q, 0), K)];
-    const float2 u = pre[p];
-    const int pn = __shfl_down_sync(FULL, p, 1);
+    const float2 u = pre[min(max(q, 0), K)];
     const float hn = __shfl_down_sync(FULL, u.x, 1), ln = __shfl_down_sync(FULL, u.y, 1);
-    if (lane < 31 && k <= kB && pn > p) f(k, __fadd_rn(__fsub_rn(hn, u.x), __fsub_rn(ln, u.y)));
+    if (lane < 31 && k <= kB) f(k, __fadd_rn(__fsub_rn(hn, u.x), __fsub_rn(ln, u.y)));
     const int x = dr - e;
     if (x > 0) { q += dq + 1; e = d - x; } else { q += dq; e = -x; }
   }
@@ -838,7 +833,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
         // NW-th), in order, into its partial totals, for CW = K / 4 classes at a time (the partials take the
         // four vectors free at this point, 4 warps x CW in each); the partials are summed in warp order
         for (int c = tid; c < nL; c += NT) RRc[c] = 0.f;  // (classes above every cell's class stay 0)
-        prefix_df(nL, [&](int b) { return L0[b]; }, pre, dred);
+        prefix_df(K, [&](int j) { return posL[j + 1] > posL[j] ? L0[posL[j]] : 0.f; }, pre, dred);  // by level
         const int jmin = LJ[0], jmax = LJ[nL - 1];
         const int CW = K / 4;
         auto bufs = [&](int w) {  // (free until the new q is formed)
@@ -856,7 +851,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
             const int kB = min(class_index(i, jmax, km1, cdiv), c0 + CW - 1);
             if (kA > kB) continue;
             const float r = R0[a];
-            line_runs_il(i, kA, kB, K, posL, pre, [&](int k, float sm) { part[k - c0] = fmaf(r, sm, part[k - c0]); });
+            line_runs_il(i, kA, kB, K, pre, [&](int k, float sm) { part[k - c0] = fmaf(r, sm, part[k - c0]); });
             __syncwarp();  // (the next row's classes may fall to other lanes)
           }
           __syncthreads();
@@ -895,12 +890,12 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
       const F rdR = scal[0], sl2 = A.printed ? (F)1.0 : scL * scL;
       if constexpr (std::is_same<F, float>::value) {
         if (runs) {  // a warp per row over its runs, column weights L^2 through their prefix sums
-          prefix_df(nL, [&](int b) { const float x = L0[b]; return x * x; }, pre, dred);
+          prefix_df(K, [&](int j) { const float x = posL[j + 1] > posL[j] ? L0[posL[j]] : 0.f; return x * x; }, pre, dred);
           const int jmin = LJ[0], jmax = LJ[nL - 1];
           for (int a = warp; a < nR; a += NW) {
             const int i = RI[a];
             float acc = 0.f;
-            line_runs(i, class_index(i, jmin, km1, cdiv), class_index(i, jmax, km1, cdiv), K, posL, pre,
+            line_runs(i, class_index(i, jmin, km1, cdiv), class_index(i, jmax, km1, cdiv), K, pre,
                       [&](int k, float sm) { acc = fmaf(q[k], sm, acc); });
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
             if (lane == 0) {
@@ -963,12 +958,12 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
       F* Bs = L2c;  // column sums (L^2 is not needed again in this iteration)
       if constexpr (std::is_same<F, float>::value) {
         if (runs) {  // a warp per column over its runs through the rows, row weights R' R by prefix sums
-          prefix_df(nR, [&](int a) { return RRc[a]; }, pre, dred);
+          prefix_df(K, [&](int i) { return posR[i + 1] > posR[i] ? RRc[posR[i]] : 0.f; }, pre, dred);  // by level
           const int imin = RI[0], imax = RI[nR - 1];
           for (int b = warp; b < nL; b += NW) {
             const int j = LJ[b];
             float acc = 0.f;
-            line_runs(j, class_index(imin, j, km1, cdiv), class_index(imax, j, km1, cdiv), K, posR, pre,
+            line_runs(j, class_index(imin, j, km1, cdiv), class_index(imax, j, km1, cdiv), K, pre,
                       [&](int k, float sm) { acc = fmaf(q[k], sm, acc); });
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
             if (lane == 0) Bs[b] = acc;
@@ -1059,7 +1054,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
       // rows' class spans go where S as a float was (not needed again)
       uint16_t* rs0 = reinterpret_cast<uint16_t*>(Sd);
       uint16_t* rs1 = rs0 + K;
-      prefix_df(nL, [&](int b) { return Lc[b]; }, pre, dred);
+      prefix_df(K, [&](int j) { return posL[j + 1] > posL[j] ? Lc[posL[j]] : 0.f; }, pre, dred);  // by level
       sl = scal[4];
       const int jmin = LJ[0], jmax = LJ[nL - 1];
       for (int a = warp; a < nR; a += NW) {
@@ -1091,14 +1086,11 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
           const int per = ((kB - kA + 32) >> 5) | 1;  // (odd: the partials' banks differ)
           const int kS = kA + lane * per, kE = min(kB, kS + per - 1);
           if (kS <= kE) {
-            int p = posL[jr[kS]];
-            float2 u = pre[p];
+            float2 u = pre[jr[kS]];
 #pragma unroll 4
             for (int k = kS; k <= kE; ++k) {
-              const int pn = posL[jr[k + 1]];
-              const float2 un = pre[pn];
-              if (pn > p) part[k - c0] = fmaf(r, __fadd_rn(__fsub_rn(un.x, u.x), __fsub_rn(un.y, u.y)), part[k - c0]);
-              p = pn;
+              const float2 un = pre[jr[k + 1]];
+              part[k - c0] = fmaf(r, __fadd_rn(__fsub_rn(un.x, u.x), __fsub_rn(un.y, u.y)), part[k - c0]);
               u = un;
             }
           }
