@@ -535,7 +535,8 @@ __device__ __forceinline__ float run_sum(const float2* pre, int p0, int p1) {
 }
 
 // The runs of classes [kA, kB] of line i (row i of the class map, or column i: the map is symmetric),
-// by a whole warp: lane l takes the l-th of 32 contiguous blocks of the classes and calls f(k, s) for
+// by a whole warp: lane l takes the l-th of 32 contiguous blocks of the classes (of odd length, so
+// per-class arrays read or updated by the lanes together fall in distinct banks) and calls f(k, s) for
 // each of its classes k, s = pre[js(i, k + 1)] - pre[js(i, k)] (pre indexed by level).  The boundary
 // js(i, k) = ceil(t / d), t = (2k - 1)(K - 1), d = 2i, is kept with its excess e = q d - t in [0, d)
 // and advanced one class at a time (t grows by 2 (K - 1)) by integer steps: one division per lane and
@@ -576,41 +577,6 @@ __device__ __forceinline__ void line_runs(int i, int kA, int kB, int K, const fl
     const float2 un = pre[min(q, K)];
     f(k, __fadd_rn(__fsub_rn(un.x, u.x), __fsub_rn(un.y, u.y)));  // (an empty run adds exactly 0)
     u = un;
-  }
-}
-
-// The same runs with lanes over 31 consecutive classes at a time (each lane's upper boundary from
-// the next lane), for callers that scatter into per-class arrays: the lanes of one step touch
-// consecutive entries (no shared-memory bank conflicts).  The boundary advances 31 classes per step.
-template <class Fn>
-__device__ __forceinline__ void line_runs_il(int i, int kA, int kB, int K, const float2* pre, Fn f) {
-  const int lane = threadIdx.x & 31;
-  if (i == 0) {
-    if (lane == 0 && kA == 0) f(0, run_sum(pre, 0, K));
-    return;
-  }
-  const int km1 = K - 1, d = 2 * i;
-  // (estimates made exact as in line_runs: dt < 2^18 exact in FP32, |t| < 2^26)
-  const float rd = __frcp_rn((float)d);
-  const int dt = 62 * km1;
-  int dq = __float2int_rz(__fmul_rn((float)dt, rd));
-  dq += (dt - dq * d >= d) - (dt - dq * d < 0);
-  const int dr = dt - dq * d;
-  const int t = (2 * (kA + lane) - 1) * km1;
-  int q = __float2int_ru(__fmul_rn((float)t, rd));
-  int e = q * d - t;
-  if (e < 0) { ++q; e += d; }
-  if (e < 0) { ++q; e += d; }
-  if (e >= d) { --q; e -= d; }
-  if (e >= d) { --q; e -= d; }
-#pragma unroll 2
-  for (int k0 = kA; k0 <= kB; k0 += 31) {
-    const int k = k0 + lane;
-    const float2 u = pre[min(max(q, 0), K)];
-    const float hn = __shfl_down_sync(FULL, u.x, 1), ln = __shfl_down_sync(FULL, u.y, 1);
-    if (lane < 31 && k <= kB) f(k, __fadd_rn(__fsub_rn(hn, u.x), __fsub_rn(ln, u.y)));
-    const int x = dr - e;
-    if (x > 0) { q += dq + 1; e = d - x; } else { q += dq; e = -x; }
   }
 }
 
@@ -851,7 +817,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs A) {
             const int kB = min(class_index(i, jmax, km1, cdiv), c0 + CW - 1);
             if (kA > kB) continue;
             const float r = R0[a];
-            line_runs_il(i, kA, kB, K, pre, [&](int k, float sm) { part[k - c0] = fmaf(r, sm, part[k - c0]); });
+            line_runs(i, kA, kB, K, pre, [&](int k, float sm) { part[k - c0] = fmaf(r, sm, part[k - c0]); });
             __syncwarp();  // (the next row's classes may fall to other lanes)
           }
           __syncthreads();
