@@ -199,6 +199,31 @@ def _geom(t):
     return int(t.shape[1]), int(t.shape[0]), int(t.stride(0)) * eb, eb
 
 
+class PreparedBatch:
+    """The argument arrays of one histretinex_enhance_batch call, marshalled once: a batch called
+    again and again on the same device buffers (a pipeline that reuses its input and output tensors)
+    then costs no per-image work in Python, which for hundreds of images takes milliseconds, longer
+    than the batch itself on the GPU.  The object keeps the tensors alive; it must not outlive a change
+    of their storage (resize_, set_)."""
+
+    def __init__(self, ins, outs=None):
+        import torch
+        if outs is None:
+            outs = [torch.empty_like(t) for t in ins]
+        n = len(ins)
+        if n != len(outs) or n == 0:
+            raise ValueError("need matching, non-empty input and output lists")
+        g = [_geom(t) for t in ins]
+        go = [_geom(t) for t in outs]
+        eb = g[0][3]
+        if any(x[3] != eb for x in g + go) or any(a[:2] != b[:2] for a, b in zip(g, go)):
+            raise ValueError("all images must share one element type and outputs must match inputs")
+        VP, I, SZ = ctypes.c_void_p * n, ctypes.c_int * n, ctypes.c_size_t * n
+        self.ins, self.outs, self.n, self.eb = list(ins), list(outs), n, eb
+        self.args = (VP(*[t.data_ptr() for t in ins]), VP(*[t.data_ptr() for t in outs]), I(*[x[0] for x in g]),
+                     I(*[x[1] for x in g]), SZ(*[x[2] for x in g]), SZ(*[x[2] for x in go]))
+
+
 def enhance_noalloc(d_in, d_out, params: "Params | None" = None, stream=None):
     """histretinex_enhance_noalloc: one device image, no context, no device allocation (K <= 256)."""
     W, H, pin, eb = _geom(d_in)
@@ -284,26 +309,12 @@ class Context:
                                           out_pitch, elem_bytes, _stream_ptr(stream)), "histretinex_enhance")
 
     def enhance_batch(self, ins, outs=None, stream=None):
-        """Enhance a list of device images with one launch per pipeline stage."""
-        import torch
-        if outs is None:
-            outs = [torch.empty_like(t) for t in ins]
-        n = len(ins)
-        if n != len(outs) or n == 0:
-            raise ValueError("need matching, non-empty input and output lists")
-        g = [_geom(t) for t in ins]
-        go = [_geom(t) for t in outs]
-        eb = g[0][3]
-        if any(x[3] != eb for x in g + go) or any(a[:2] != b[:2] for a, b in zip(g, go)):
-            raise ValueError("all images must share one element type and outputs must match inputs")
-        VP = ctypes.c_void_p * n
-        I = ctypes.c_int * n
-        SZ = ctypes.c_size_t * n
-        _check(_lib().histretinex_enhance_batch(
-            self._h, n, VP(*[t.data_ptr() for t in ins]), VP(*[t.data_ptr() for t in outs]), I(*[x[0] for x in g]),
-            I(*[x[1] for x in g]), SZ(*[x[2] for x in g]), SZ(*[x[2] for x in go]), eb, _stream_ptr(stream)),
-            "histretinex_enhance_batch")
-        return outs
+        """Enhance a list of device images with one launch per pipeline stage.  `ins` may instead be a
+        PreparedBatch (then `outs` is not given): its arrays are passed as they are."""
+        pb = ins if isinstance(ins, PreparedBatch) else PreparedBatch(ins, outs)
+        _check(_lib().histretinex_enhance_batch(self._h, pb.n, *pb.args, pb.eb, _stream_ptr(stream)),
+               "histretinex_enhance_batch")
+        return pb.outs
 
     def enhance_host(self, h_in, h_out=None, stream=None):
         """End to end from host memory: numpy arrays or (pinned) CPU tensors, (H, W, 3) uint8/uint16."""

@@ -209,3 +209,19 @@ def test_two_group_batch_equals_one_group(hr):
     two.check()
     for i in (3, 200):
         assert np.array_equal(o2b[i].cpu().numpy(), o2[i].cpu().numpy())
+
+
+def test_prepared_batch_equals_the_list_call(hr):
+    """A batch whose arguments were marshalled once (PreparedBatch), called twice, gives the pixels
+    the same images get through the list form of enhance_batch."""
+    import torch
+    imgs = mixed_images(7, seed=11)
+    ctx = hr.Context(hr.Params())
+    ins = [torch.from_numpy(im).cuda() for im in imgs]
+    want = [o.cpu().numpy() for o in ctx.enhance_batch(ins)]
+    pb = hr.PreparedBatch(ins)
+    for _ in range(2):
+        got = ctx.enhance_batch(pb)
+        ctx.check()
+        for a, b in zip(got, want):
+            assert np.array_equal(a.cpu().numpy(), b)

@@ -83,3 +83,21 @@ def test_set_tuning_validation_without_a_device():
     t = hr.hr_tuning(8, 16, 16, 1, 5, 2)
     # a null context is an argument error whatever the record says
     assert lib.histretinex_set_tuning(None, ctypes.byref(t)) == hr.ERR_INVALID_ARG
+
+
+def test_prepared_batch_argument_checks():
+    """PreparedBatch marshals a batch's arguments once and refuses what enhance_batch refuses."""
+    import torch
+    import paper_2510_21100_gb300 as hr
+    a = torch.zeros((4, 6, 3), dtype=torch.uint8)
+    b = torch.zeros((5, 7, 3), dtype=torch.uint8)
+    pb = hr.PreparedBatch([a, b], [torch.zeros_like(a), torch.zeros_like(b)])
+    assert pb.n == 2 and pb.eb == 1 and list(pb.args[2]) == [6, 7] and list(pb.args[3]) == [4, 5]
+    assert list(pb.args[4]) == [18, 21]
+    import pytest
+    with pytest.raises(ValueError):
+        hr.PreparedBatch([a], [torch.zeros_like(b)])          # output shape differs
+    with pytest.raises(ValueError):
+        hr.PreparedBatch([a, b.to(torch.int16)[..., :3]])      # element type
+    with pytest.raises(ValueError):
+        hr.PreparedBatch([], [])
