@@ -277,6 +277,15 @@ __device__ __forceinline__ unsigned hfma2(unsigned a, unsigned b, unsigned c) {
 // Shared-memory count without a compiler memory barrier: the histograms are read only after the
 // warp and block barriers at a warp's image change and at the kernel's end.
 __device__ __forceinline__ void red_sh(unsigned addr) { asm volatile("red.shared.add.u32 [%0], 1;\n" ::"r"(addr)); }
+// The same count when `on` holds, as one predicated instruction (no branch around it).
+__device__ __forceinline__ void red_sh_if(unsigned addr, bool on) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %1, 0;\n@p red.shared.add.u32 [%0], 1;\n}\n" ::"r"(addr),
+               "r"((unsigned)on));
+}
+// Takes one count back (adds 2^32 - 1).
+__device__ __forceinline__ void unred_sh(unsigned addr) {
+  asm volatile("red.shared.add.u32 [%0], 0xffffffff;\n" ::"r"(addr));
+}
 __device__ __forceinline__ void cp_async16s(unsigned dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
 }
@@ -327,6 +336,8 @@ struct SegLane {
   unsigned sel0, sel1, sel2;  // byte selectors of the neighbour pixel's three channels
   int cnt;          // pixels of the lane inside the image: W - (x0 + 16 lane)
   int rowbytes;     // 3 W
+  int eo[3], eb[3]; // edge runs: the row offset and the bytes inside the row of the lane's chunks c, c + 32,
+                    // c + 64 (offset 0 where none is inside; the rest of each chunk is zero-filled)
   bool lane0, lane31, left_nb, right_nb, use_nb;
 };
 
@@ -348,10 +359,7 @@ __device__ __forceinline__ void roll_issue(const SegLane& s, unsigned slot, int 
       cp_async16s(dst + 1024, src + 1024);
     } else {
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const int b = min(max(s.rowbytes - (s.goff + 512 * i), 0), 16);
-        cp_async16zs(dst + 512 * i, b > 0 ? (const void*)(src + 512 * i) : (const void*)row, b);
-      }
+      for (int i = 0; i < 3; ++i) cp_async16zs(dst + 512 * i, row + s.eo[i], s.eb[i]);
     }
     if (s.xbytes > 0) cp_async16zs(slot + s.sxo, row + s.xoff, s.xbytes);
   }
@@ -363,6 +371,20 @@ template <bool kEdge, bool kClamp>
 __device__ __forceinline__ void roll_build(HRow& v, const SegLane& s, const unsigned char* slotp, bool count,
                                            unsigned hs_sh, unsigned kk, bool& bad) {
   unsigned u[8];  // u[2w] = pixels (4w, 4w + 2), u[2w + 1] = pixels (4w + 1, 4w + 3): V as 16-bit pairs
+  if (kEdge && s.cnt > 0 && s.cnt < 16) {
+    // the lane holding the image's last pixel: the first pixel beyond it (zero-filled) takes a copy of
+    // it (the replicated border of the Sobel operator), and the count that copy adds is taken back
+    unsigned char* lp = const_cast<unsigned char*>(slotp) + s.roff + 3 * (s.cnt - 1);
+    const unsigned c0 = lp[0], c1 = lp[1], c2 = lp[2];
+    lp[3] = (unsigned char)c0;
+    lp[4] = (unsigned char)c1;
+    lp[5] = (unsigned char)c2;
+    if (count) {
+      unsigned vl = max(max(c0, c1), c2);
+      if (kClamp) vl = min(vl, kk & 0xffffu);
+      unred_sh(hs_sh + (vl << 2));
+    }
+  }
   {
     const uint4* q = reinterpret_cast<const uint4*>(slotp + s.roff);
     const uint4 a = q[0], b = q[1], c = q[2];
@@ -370,10 +392,6 @@ __device__ __forceinline__ void roll_build(HRow& v, const SegLane& s, const unsi
     vpairs(a.w, b.x, b.y, u[2], u[3]);
     vpairs(b.z, b.w, c.x, u[4], u[5]);
     vpairs(c.y, c.z, c.w, u[6], u[7]);
-  }
-  if (kEdge && s.cnt <= 0) {
-#pragma unroll
-    for (int w = 0; w < 8; ++w) u[w] = 0u;
   }
   if (kClamp) {  // K < 256: levels above K - 1 are a range error, clamped so counting stays in bounds
 #pragma unroll
@@ -383,27 +401,13 @@ __device__ __forceinline__ void roll_build(HRow& v, const SegLane& s, const unsi
       u[w] = c;
     }
   }
-  if (count) {
+  if (count) {  // (edge runs count the zero-filled pixels beyond the image too: level 0, taken back per run)
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-      const bool on0 = !kEdge || 4 * w < s.cnt, on1 = !kEdge || 4 * w + 1 < s.cnt;
-      const bool on2 = !kEdge || 4 * w + 2 < s.cnt, on3 = !kEdge || 4 * w + 3 < s.cnt;
-      if (on0) red_sh(hs_sh + ((u[2 * w] & 0xffffu) << 2));
-      if (on2) red_sh(hs_sh + (u[2 * w] >> 14));  // 0x00VV00WW >> 14 = VV << 2
-      if (on1) red_sh(hs_sh + ((u[2 * w + 1] & 0xffffu) << 2));
-      if (on3) red_sh(hs_sh + (u[2 * w + 1] >> 14));
-    }
-  }
-  if (kEdge && s.cnt > 0 && s.cnt < 16) {  // the pixel right of the image's last one replicates it
-    const unsigned char* lp = slotp + s.roff + 3 * (s.cnt - 1);
-    unsigned vl = max(max((unsigned)lp[0], (unsigned)lp[1]), (unsigned)lp[2]);
-    if (kClamp) vl = min(vl, kk & 0xffffu);
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      if (4 * w == s.cnt) u[2 * w] = (u[2 * w] & 0xffff0000u) | vl;
-      if (4 * w + 2 == s.cnt) u[2 * w] = (u[2 * w] & 0x0000ffffu) | (vl << 16);
-      if (4 * w + 1 == s.cnt) u[2 * w + 1] = (u[2 * w + 1] & 0xffff0000u) | vl;
-      if (4 * w + 3 == s.cnt) u[2 * w + 1] = (u[2 * w + 1] & 0x0000ffffu) | (vl << 16);
+      red_sh(hs_sh + ((u[2 * w] & 0xffffu) << 2));
+      red_sh(hs_sh + (u[2 * w] >> 14));  // 0x00VV00WW >> 14 = VV << 2
+      red_sh(hs_sh + ((u[2 * w + 1] & 0xffffu) << 2));
+      red_sh(hs_sh + (u[2 * w + 1] >> 14));
     }
   }
 #pragma unroll
@@ -456,10 +460,17 @@ __device__ __forceinline__ void roll_sobel(const HRow& T, const HRow& M, const H
     m2_pair(gxO, gyO, m1, m3);
     const unsigned b0 = grad_bits_f(m0, mclipf), b1 = grad_bits_f(m1, mclipf);
     const unsigned b2 = grad_bits_f(m2, mclipf), b3 = grad_bits_f(m3, mclipf);
-    if (!kEdge || 4 * w < cnt) red_sh(hg_adj + (b0 << 2));
-    if (!kEdge || 4 * w + 1 < cnt) red_sh(hg_adj + (b1 << 2));
-    if (!kEdge || 4 * w + 2 < cnt) red_sh(hg_adj + (b2 << 2));
-    if (!kEdge || 4 * w + 3 < cnt) red_sh(hg_adj + (b3 << 2));
+    if (!kEdge) {
+      red_sh(hg_adj + (b0 << 2));
+      red_sh(hg_adj + (b1 << 2));
+      red_sh(hg_adj + (b2 << 2));
+      red_sh(hg_adj + (b3 << 2));
+    } else {
+      red_sh_if(hg_adj + (b0 << 2), 4 * w < cnt);
+      red_sh_if(hg_adj + (b1 << 2), 4 * w + 1 < cnt);
+      red_sh_if(hg_adj + (b2 << 2), 4 * w + 2 < cnt);
+      red_sh_if(hg_adj + (b3 << 2), 4 * w + 3 < cnt);
+    }
     csOp = csOc; ddOp = ddOc; csEc = csEn; ddEc = ddEn;
   }
 }
@@ -551,7 +562,13 @@ __global__ void __launch_bounds__(kHT, 2) hist_u8s_kernel(const ImgTab tab, int 
   int cur = -1, img_u0 = 0, img_u1 = 0, nb = 1;
   ImageDesc im{};
   bool bad = false;
+  // zero-filled pixels beyond the right edge that this warp's edge runs counted at level 0 of the
+  // current image (warp-uniform)
+  unsigned phantom = 0;
   auto flush_warp = [&](int im_idx) {
+    __syncwarp();
+    if (lane == 0) hist[warp][0][0] -= phantom;
+    phantom = 0;
     __syncwarp();
     unsigned* S = reinterpret_cast<unsigned*>(slots + (size_t)im_idx * slot_bytes + lay.S);
     unsigned* G = reinterpret_cast<unsigned*>(slots + (size_t)im_idx * slot_bytes + lay.G);
@@ -603,13 +620,26 @@ __global__ void __launch_bounds__(kHT, 2) hist_u8s_kernel(const ImgTab tab, int 
     s.xoff = lane == 0 ? 3 * x0 - 16 : 3 * (x0 + kStripW);
     s.xbytes = lane == 0 ? (s.left_nb ? 16 : 0) : (lane == 1 ? min(max(rb, 0), 16) : 0);
     s.use_nb = (s.lane0 && s.left_nb) || (s.lane31 && s.right_nb);
-    if (all_edge || x0 + kStripW > im.W)
+    if (all_edge || x0 + kStripW > im.W) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        s.eb[i] = min(max(s.rowbytes - (s.goff + 512 * i), 0), 16);
+        s.eo[i] = s.eb[i] > 0 ? s.goff + 512 * i : 0;
+      }
+      // every counted row adds kStripW - w pixels of level 0 beyond the image (w = W - x0 pixels
+      // inside), less the one that replicates the border (counted, and taken back, at its own level)
+      const int w = im.W - x0;
+      if (w < kStripW) phantom += (unsigned)(yb - ya) * (unsigned)(kStripW - w - ((w & 15) ? 1 : 0));
       bad |= roll_run_edge<kClamp>(s, ya, yb, wring, wring_sh, hs_sh, hg_adj, mclipf, kk);
-    else
+    } else
       bad |= roll_run<false, kClamp>(s, ya, yb, wring, wring_sh, hs_sh, hg_adj, mclipf, kk);
   }
   // the warps' last images: sum the warps that share an image, one global add per level
-  if (lane == 0) warp_img[warp] = cur;
+  __syncwarp();
+  if (lane == 0) {
+    hist[warp][0][0] -= phantom;
+    warp_img[warp] = cur;
+  }
   __syncthreads();
   for (int idx = tid; idx < 2 * kHBins; idx += kHT) {
     const int which = idx / kHBins, k = idx % kHBins;

@@ -7,7 +7,9 @@ budget allows (input + output image + per-image workspace), copies them to the d
 stream, and launches one batched pipeline call for them; batches on different streams overlap
 on the device, and requests arriving while others run are admitted as soon as a stream and
 memory free up.  Results stay resident on the device.  Each request's latency runs from its
-arrival time to the completion of its batch.
+arrival time to the completion of its batch.  The statistics also give the longest iteration of
+the host loop that did not wait on the device on purpose: when the serving process itself is held
+up (descheduled, or stuck in the operating system), that lag says so.
 """
 from __future__ import annotations
 
@@ -40,6 +42,7 @@ class ServeStats:
     latencies_ms: list = field(default_factory=list)
     batches: int = 0
     max_batch: int = 0
+    max_loop_lag_ms: float = 0.0
 
     def percentile(self, q: float) -> float:
         v = sorted(self.latencies_ms)
@@ -49,9 +52,10 @@ class ServeStats:
         return v[k]
 
     def summary(self) -> dict:
-        return {"requests": self.completed, "seconds": self.seconds, "MP_per_s": self.megapixels / self.seconds,
+        mps = self.megapixels / self.seconds if self.seconds > 0 else 0.0
+        return {"requests": self.completed, "seconds": self.seconds, "MP_per_s": mps,
                 "p50_ms": self.percentile(50), "p99_ms": self.percentile(99), "batches": self.batches,
-                "max_batch": self.max_batch}
+                "max_batch": self.max_batch, "max_loop_lag_ms": self.max_loop_lag_ms}
 
 
 def window_stats(requests, start: float, end: float | None = None) -> dict:
@@ -154,8 +158,10 @@ class Server:
         max_b = 0
         t0 = time.perf_counter()
         done: list[Request] = []
+        lag = 0.0  # longest loop iteration, less its intended sleep, that did not wait on the device
         while len(done) < len(pending):
             now = time.perf_counter() - t0
+            waited = False
             while nxt < len(pending) and pending[nxt].arrival <= now:
                 queue.append(pending[nxt])
                 nxt += 1
@@ -203,15 +209,21 @@ class Server:
             if inflight and (not free_streams or not queue):
                 if nxt >= len(pending) and not queue:
                     inflight[0][1].synchronize()  # nothing left to admit: wait for the oldest batch
+                    waited = True
                 else:
                     time.sleep(poll_sleep)
+                    now += poll_sleep
             elif not inflight and not queue and nxt < len(pending):
-                time.sleep(min(poll_sleep, max(0.0, pending[nxt].arrival - (time.perf_counter() - t0))))
-        seconds = max(r.done for r in done)
+                nap = min(poll_sleep, max(0.0, pending[nxt].arrival - (time.perf_counter() - t0)))
+                time.sleep(nap)
+                now += nap
+            if not waited:
+                lag = max(lag, time.perf_counter() - t0 - now)
+        seconds = max((r.done for r in done), default=0.0)
         for ctx in self.ctxs:
             ctx.check()
         lat = [(r.done - r.arrival) * 1e3 for r in done]
-        return ServeStats(len(done), seconds, sum(r.megapixels for r in done), lat, batches, max_b)
+        return ServeStats(len(done), seconds, sum(r.megapixels for r in done), lat, batches, max_b, lag * 1e3)
 
     def close(self):
         for c in self.ctxs:

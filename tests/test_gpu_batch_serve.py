@@ -129,7 +129,7 @@ def test_server_results_identical_alone_and_in_the_mix(hr):
         k = next(i for i, p in enumerate(pool) if p is r.image)
         assert np.array_equal(r.out.cpu().numpy(), alone[k])
     s = stats.summary()
-    assert s["p99_ms"] >= s["p50_ms"] > 0
+    assert s["p99_ms"] >= s["p50_ms"] > 0 and s["max_loop_lag_ms"] >= 0
     srv.close()
 
 
@@ -145,6 +145,8 @@ def test_server_respects_the_memory_budget(hr):
     reqs = [serve.Request(i, 0.0, img) for i in range(6)]
     st = srv2.run(reqs)
     assert st.completed == 6 and st.max_batch <= 2
+    st0 = srv2.run([])
+    assert st0.completed == 0 and st0.batches == 0 and st0.summary()["MP_per_s"] == 0.0
     srv.close(); srv2.close()
 
 

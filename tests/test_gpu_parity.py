@@ -219,11 +219,14 @@ def test_large_batch_takes_strip_histograms(hr):
     """A batch with enough 512 x 4 strips for the rolling strip histogram kernel, whose warps take
     equal runs of strip rows column by column, across image boundaries (interior and partial right
     columns on their two code paths): every image gets the histograms, LUT and pixels it gets alone,
-    and a few are checked against the oracle."""
+    and a few are checked against the oracle.  Partial columns count the zero-filled pixels beyond the
+    border at level 0 and take them back per warp, so S is the strongest check of that path."""
     import torch
     from gpu_util import assert_close
     ctx, po = ctx_for(hr)
-    sizes = [(1500, 1000), (1283, 725), (700, 333), (512, 480), (1024, 769), (95, 33), (1, 1), (2047, 1031)] * 4
+    # (1056 and 528: partial last columns of whole 16-pixel lanes, no lane straddling the border)
+    sizes = [(1500, 1000), (1283, 725), (700, 333), (512, 480), (1024, 769), (95, 33), (1, 1), (2047, 1031),
+             (1056, 601), (528, 77)] * 4
     assert sum(-(-w // 512) * -(-h // 4) for w, h in sizes) >= 2 * 152 * 16
     imgs = [synth.low_light_image(w, h, seed=5100 + i) for i, (w, h) in enumerate(sizes)]
     dins = [hr.to_device_aligned(im) for im in imgs]
@@ -239,7 +242,7 @@ def test_large_batch_takes_strip_histograms(hr):
         for k in ("R", "L", "T"):
             assert_close(dbg_b[k], dbg_s[k], k)
         assert np.array_equal(out_b, out_s), i
-    for i in (0, 2, 7):
+    for i in (0, 2, 7, 8, 9):
         compare_to_oracle(imgs[i], batch[i][0], batch[i][1], po)
 
 

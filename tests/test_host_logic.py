@@ -50,7 +50,10 @@ def test_serve_stats_percentiles_and_summary():
     assert st.percentile(50) == 50 and st.percentile(99) == 99 and st.percentile(100) == 100
     s = st.summary()
     assert s["MP_per_s"] == 25.0 and s["p50_ms"] == 50 and s["p99_ms"] == 99 and s["max_batch"] == 5
+    assert s["max_loop_lag_ms"] == 0.0
     assert math.isnan(serve.ServeStats(0, 1.0, 0.0).percentile(50))
+    empty = serve.ServeStats(0, 0.0, 0.0).summary()
+    assert empty["requests"] == 0 and empty["MP_per_s"] == 0.0 and math.isnan(empty["p99_ms"])
 
 
 def test_mixed_batch_sizes_span_the_stated_range():
