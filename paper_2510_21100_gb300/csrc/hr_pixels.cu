@@ -849,9 +849,10 @@ __global__ void __launch_bounds__(kThreads, 8) apply_u8v_kernel(const ImgTab tab
   pdl_trigger();  // the next one may be scheduled (it waits for this one)
   const int n = tab.n;
   const int* __restrict__ tile_start = tab.tiles;  // (n > 1 only)
-  // per level V: out_c = (c F_V + B_V) >> 18 with F_V = ceil(V' 2^18 / V), B_V = 2^17, which is
-  // floor(c V'/V + 1/2) exactly for c <= V < 256 (the product is at most V' 2^18 + V < 2^32 and
-  // overshoots by at most c / 2^18 < 1/(2V)); V = 0 gives F = 0, B = V' << 18.
+  // per level V: out_c = (c F_V + B_V) >> 24 with F_V = ceil(V' 2^24 / V), B_V = 2^23, which is
+  // floor(c V'/V + 1/2) exactly for c <= V < 256 (the sum is below V' 2^24 + V + 2^23 < 2^32 and
+  // overshoots by at most c / 2^24 < 1/(2V)); V = 0 gives F = 0, B = V' << 24.  The result sits in
+  // the top byte, so four of them go into an output word with three byte permutes.
   __shared__ uint2 fb[256];
   const int tid = threadIdx.x;
   const int chunk = (total + gridDim.x - 1) / gridDim.x;
@@ -868,7 +869,7 @@ __global__ void __launch_bounds__(kThreads, 8) apply_u8v_kernel(const ImgTab tab
       const unsigned short* gl = reinterpret_cast<const unsigned short*>(slots + (size_t)img * slot_bytes + lay.lut);
       for (int k = tid; k < 256; k += kThreads) {
         const unsigned vp = k < K ? gl[k] : 0u;
-        fb[k] = k == 0 ? make_uint2(0u, vp << 18) : make_uint2(((vp << 18) + (unsigned)k - 1u) / (unsigned)k, 1u << 17);
+        fb[k] = k == 0 ? make_uint2(0u, vp << 24) : make_uint2(((vp << 24) + (unsigned)k - 1u) / (unsigned)k, 1u << 23);
       }
       __syncthreads();
       im = tab.desc(img);
@@ -893,25 +894,26 @@ __global__ void __launch_bounds__(kThreads, 8) apply_u8v_kernel(const ImgTab tab
       const unsigned w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
       unsigned o[12];
 #pragma unroll
-      for (int q = 0; q < 12; ++q) o[q] = 0u;
+      for (int g = 0; g < 4; ++g) {  // four pixels: output words 3g .. 3g + 2
+        unsigned t[12];              // output byte 12 g + b in the top byte of t[b]
 #pragma unroll
-      for (int p = 0; p < 16; ++p) {
-        unsigned ch[3];
+        for (int p = 0; p < 4; ++p) {
+          unsigned ch[3];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) ch[q] = __byte_perm(w[(3 * p + q) >> 2], 0u, 0x4440 + ((3 * p + q) & 3));
-        unsigned V = __vimax3_u32(ch[0], ch[1], ch[2]);
-        if (!kAll) {
-          range_bad |= V > vmax;
-          V = min(V, vmax);
+          for (int q = 0; q < 3; ++q) ch[q] = __byte_perm(w[3 * g + ((3 * p + q) >> 2)], 0u, 0x4440 + ((3 * p + q) & 3));
+          unsigned V = __vimax3_u32(ch[0], ch[1], ch[2]);
+          if (!kAll) {
+            range_bad |= V > vmax;
+            V = min(V, vmax);
+          }
+          const uint2 f = fb[V];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) t[3 * p + q] = ch[q] * f.x + f.y;
         }
-        const uint2 f = fb[V];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          // byte j of the output word: ((c F + B) >> 18) << 8 j, as one shift and a mask (c F + B < 2^26)
-          const unsigned t = ch[q] * f.x + f.y;
-          const int j = (3 * p + q) & 3;
-          o[(3 * p + q) >> 2] |= (j < 3 ? t >> (18 - 8 * j) : t << (8 * j - 18)) & (0xffu << (8 * j));
-        }
+        for (int q = 0; q < 3; ++q)
+          o[3 * g + q] = __byte_perm(__byte_perm(t[4 * q], t[4 * q + 1], 0x0073),
+                                     __byte_perm(t[4 * q + 2], t[4 * q + 3], 0x0073), 0x5410);
       }
       uint4* d4 = reinterpret_cast<uint4*>(dst);
       d4[0] = make_uint4(o[0], o[1], o[2], o[3]);
@@ -924,7 +926,7 @@ __global__ void __launch_bounds__(kThreads, 8) apply_u8v_kernel(const ImgTab tab
         range_bad |= V > vmax;
         V = min(V, vmax);
         const uint2 f = fb[V];
-        for (int q = 0; q < 3; ++q) dst[3 * p + q] = (unsigned char)((ch[q] * f.x + f.y) >> 18);
+        for (int q = 0; q < 3; ++q) dst[3 * p + q] = (unsigned char)((ch[q] * f.x + f.y) >> 24);
       }
     }
   }
