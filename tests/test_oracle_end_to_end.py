@@ -64,3 +64,28 @@ def test_uint16_12bit_pipeline_runs_and_brightens():
     assert r.out.dtype == np.uint16 and int(r.out.max()) < 4096
     assert r.out.max(axis=2).mean() > img.max(axis=2).mean()
     assert abs(r.T.sum() - 64 * 48) / (64 * 48) < 1e-12
+
+
+@pytest.mark.parametrize("bits,K", [(8, 256), (12, 4096)])
+def test_mirrored_tiling_scales_every_histogram_and_keeps_lut_and_pixels(bits, K):
+    """Invariance the method implies: an image made of 2 x 2 blocks [T, T mirrored left-right; T
+    mirrored top-bottom, T mirrored both ways] gives every pixel the 3 x 3 neighbourhood (mirrored) it
+    has in T with the replicated border, so H_C(S) and H_C(grad S) are n times T's (n tiles); Eq. 11-15
+    and Eq. 17-20 are homogeneous of degree one in (S, G, R, L, N), and with n a power of two the FP64
+    scaling is exact, so R, L and the target are n times T's bit for bit, the LUT is T's, and the
+    output is the same tiling of T's output.  (A border other than the replicated one, or a term of
+    another degree, breaks it.)"""
+    t = synth.low_light_image(37, 29, seed=5, bits=bits)
+    top = np.concatenate([t, t[:, ::-1]], axis=1)
+    blk = np.concatenate([top, top[::-1]], axis=0)
+    big = np.ascontiguousarray(np.tile(blk, (2, 4, 1)))
+    n = 32
+    r = oracle.enhance(t, oracle.Params(K=K))
+    rb = oracle.enhance(big, oracle.Params(K=K))
+    assert np.array_equal(rb.S, n * r.S) and np.array_equal(rb.G, n * r.G)
+    for a, b in ((rb.R, r.R), (rb.L, r.L), (rb.T, r.T)):
+        assert np.array_equal(a / n, b)
+    assert np.array_equal(rb.lut, r.lut)
+    wo = np.concatenate([r.out, r.out[:, ::-1]], axis=1)
+    wo = np.concatenate([wo, wo[::-1]], axis=0)
+    assert np.array_equal(rb.out, np.tile(wo, (2, 4, 1)))
