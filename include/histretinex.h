@@ -281,7 +281,8 @@ hr_status histretinex_profile_solve(hr_ctx* ctx, int image, long long* ns, int* 
  * range beyond the form's; HR_ERR_CUDA if the launch fails. */
 hr_status histretinex_gradient_levels(int form, int K, int m2_first, int n, uint16_t* d_out, void* stream);
 
-/* Measured ablation of the reduced-precision form (north_star "Precision"), not part of the paper's
+/* Measured ablation of the reduced-precision form (the K x K products batched across images as a
+ * dense contraction on the tensor cores), not part of the paper's
  * method and not on the enhancement path: the Eq. 11 class totals P_n[k] = sum over the cells
  * (i, j) of class k (index(i, j) = round(i j / (K - 1)), definition under Eq. 10) of R_n[i] L_n[j]
  * (the count matrix of Eq. 6 without its 1/N) for n images at once.  method 0: an FP32 gather on the
