@@ -20,6 +20,7 @@
 // others at three cluster barriers per iteration.  The summation order differs from a
 // left-to-right loop; sums of non-negative terms then agree to a few ulps per term.
 #include <cooperative_groups.h>
+#include <atomic>
 #include <type_traits>
 
 #include "hr_internal.cuh"
@@ -1353,12 +1354,19 @@ cudaError_t launch_solve_t(const SolveArgs& a0, int n, int cluster, cudaStream_t
   e = cudaFuncSetAttribute(solve_kernel<F>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   // the requested cluster per image (vectors must be in shared memory), capped at what can be
-  // resident
-  static int cached_K = -1, cached_max = 1;
+  // resident; that cap is found once per K (it depends on K and F alone) and kept in an atomic
+  // entry per log2 K, 0 until found, so contexts used from several host threads read whole values
+  static std::atomic<int> cluster_cap[13];
   int C = 1;
   if (a.vec_in_smem && cluster > 1) {
-    if (cached_K != a.K) { cached_max = solve_cluster_size<F>(smem); cached_K = a.K; }
-    C = cluster < cached_max ? cluster : cached_max;
+    int lk = 0;
+    while ((1 << lk) < a.K) ++lk;
+    int cap = cluster_cap[lk].load(std::memory_order_relaxed);
+    if (cap == 0) {
+      cap = solve_cluster_size<F>(smem);
+      cluster_cap[lk].store(cap, std::memory_order_relaxed);
+    }
+    C = cluster < cap ? cluster : cap;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n * C));
