@@ -989,18 +989,26 @@ cudaError_t launch_hist(const ImgTab& tab, int total_tiles, int total_units, int
   int grid = sms * ctas_per_sm;
   if (grid > total_tiles) grid = total_tiles;
   if (grid < 1) grid = 1;
+  // Each kernel's dynamic shared-memory limit is set to the most any call of it takes (K = 256 for the
+  // 8-bit kernels, K = 4096 for the generic one), the same value on every call, so calls of contexts
+  // on several host threads cannot lower it under each other's launches; a launch still takes only
+  // its own size.
   if (elem_bytes == 1 && fast) {
     const size_t smem_v = (size_t)2 * kWarps * K * sizeof(unsigned) + (size_t)kVH * kVTS + (size_t)2 * kVH * kRawRow;
-    cudaFuncSetAttribute(hist_u8v_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_v);
+    const size_t smem_v_max = (size_t)2 * kWarps * kHBins * sizeof(unsigned) + (size_t)kVH * kVTS + (size_t)2 * kVH * kRawRow;
+    cudaFuncSetAttribute(hist_u8v_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_v_max);
     return launch_kernel(hist_u8v_kernel, dim3(grid), dim3(kThreads), smem_v, st, pdl, tab, total_tiles, K, slots,
                          slot_bytes, lay, status);
   }
+  // (K <= 256: kWarps copies of K bins; above: one copy of up to 4096)
+  const size_t smem_max = std::max((size_t)2 * kWarps * kHBins, (size_t)2 * 4096) * sizeof(unsigned) +
+                          (size_t)kVH * kVW * sizeof(unsigned short);
   if (elem_bytes == 1) {
-    cudaFuncSetAttribute(hist_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(hist_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
     return launch_kernel(hist_kernel<uint8_t>, dim3(grid), dim3(kThreads), smem, st, pdl, tab, total_tiles, K, slots,
                          slot_bytes, lay, status, (int)forward, shift, M);
   }
-  cudaFuncSetAttribute(hist_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(hist_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
   return launch_kernel(hist_kernel<uint16_t>, dim3(grid), dim3(kThreads), smem, st, pdl, tab, total_tiles, K, slots,
                        slot_bytes, lay, status, (int)forward, shift, M);
 }

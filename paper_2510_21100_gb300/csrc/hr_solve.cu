@@ -20,6 +20,7 @@
 // others at three cluster barriers per iteration.  The summation order differs from a
 // left-to-right loop; sums of non-negative terms then agree to a few ulps per term.
 #include <cooperative_groups.h>
+#include <algorithm>
 #include <atomic>
 #include <type_traits>
 
@@ -1349,7 +1350,14 @@ cudaError_t launch_solve_t(const SolveArgs& a0, int n, int cluster, cudaStream_t
   a.list_in_smem = a.K <= 1024 ? 1 : 0;
   a.vec_in_smem = solve_smem_bytes(a.K, 1, a.list_in_smem, sizeof(F)) <= kSmemMax ? 1 : 0;
   const size_t smem = solve_smem_bytes(a.K, a.vec_in_smem, a.list_in_smem, sizeof(F));
-  cudaError_t e = cudaFuncSetAttribute(solve_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the kernel's dynamic shared-memory limit: the most any K takes, the same value on every call, so
+  // calls of contexts on several host threads cannot lower it under each other's launches
+  size_t smem_max = 0;
+  for (int k = 8; k <= 4096; k <<= 1) {
+    const int list = k <= 1024 ? 1 : 0, vec = solve_smem_bytes(k, 1, list, sizeof(F)) <= kSmemMax ? 1 : 0;
+    smem_max = std::max(smem_max, solve_smem_bytes(k, vec, list, sizeof(F)));
+  }
+  cudaError_t e = cudaFuncSetAttribute(solve_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(solve_kernel<F>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
